@@ -1,0 +1,493 @@
+/*
+ * ltpc_oracle.c -- plain, slow, FP64 CPU oracle for the collision hot path of
+ * "A Portable Multi-GPU Solver for Collisional Plasmas with Coulombic
+ * Interactions" (Almgren-Bell et al., arXiv 2508.06771).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  The product path (the CUDA
+ * library of the package) never calls it, and the two share no code, header,
+ * table or constant generator.  Physical constants and per-cell parameters
+ * arrive as arguments from the workload generator.
+ *
+ * Everything below is sequential FP64 in the order the paper states its steps.
+ * It is compiled with -ffp-contract=off so that no fused multiply-add changes
+ * the rounding of any expression written here.
+ *
+ * Pinning status (what each function is checked against in tests/):
+ *   orc_philox4x32_10   known-answer vectors of Philox4x32-10 + chi^2 uniformity
+ *   orc_group           numpy stable argsort / bincount
+ *   orc_pair_order      brute force with an independent Python Philox
+ *   orc_ta_pair         rotation invariants, conservation, angle statistics
+ *   orc_coulomb         conservation, Maxwellian stationarity, NRL relaxation
+ *   orc_neutral         analytic collision counts, energy bookkeeping
+ *   orc_moments         numpy bincount sums
+ *   orc_nrl_lnlambda    hand-evaluated formulary values
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+/* Random-stream tags: which use a Philox block serves (counter word 2). */
+enum { ORC_TAG_PARTICLE = 1, ORC_TAG_PAIR = 2, ORC_TAG_SCATTER = 3, ORC_TAG_SECONDARY = 4 };
+
+/* Error codes (same numeric meaning as the library's, defined independently). */
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ECAPACITY = -2 };
+
+typedef struct {
+    double mass;         /* electron mass m [kg]                         */
+    double charge;       /* elementary charge e [C]                      */
+    double eps0;         /* vacuum permittivity [F/m]                    */
+    double weight;       /* macro-particle weight w (uniform, Sec. 8)    */
+    double n_neutral;    /* neutral density n_n [1/m^3]                  */
+    double mass_neutral; /* neutral mass M [kg]                          */
+    double sigma_el;     /* constant elastic cross section [m^2]         */
+    double sigma_ion;    /* ionization cross section above threshold     */
+    double e_ion;        /* ionization threshold [eV]                    */
+    uint64_t seed;       /* Philox key                                   */
+    int32_t odd_mode;    /* 0: last particle of an odd cell sits out     */
+    int32_t correction;  /* 1: restore per-cell momentum+energy after TA */
+} orc_params;
+
+/* ------------------------------------------------------------------------- *
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random numbers:
+ * as easy as 1, 2, 3").  Ten rounds of the Philox S-box on a 4x32-bit counter
+ * with a 2x32-bit key; the key is advanced by the Weyl constants between
+ * rounds.  The paper's kernels draw uniforms with cupy.random.rand
+ * (Sec. 4.2, Sec. 4.4); this build replaces that with counter-based draws.
+ * ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* One block of four words for stream `tag` of particle (or pair) id `id` at
+ * time step `step`: counter = (id lo, step, tag, id hi), key = seed. */
+static void orc_draw(uint64_t seed, uint64_t id, uint32_t step, uint32_t tag, uint32_t w[4])
+{
+    uint32_t ctr[4] = {(uint32_t)id, step, tag, (uint32_t)(id >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, w);
+}
+
+/* FP64 uniform on (0,1): (w + 1/2) 2^-32, exact in double, never 0 or 1. */
+double orc_uniform(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+/* ------------------------------------------------------------------------- *
+ * Per-cell grouping, Table 5 steps CCS1-CCS3: N_j = |P_j| (CCS1), start
+ * offsets I_j by an exclusive prefix sum over N_j (CCS2), and the index array
+ * P holding every cell's particles contiguously (CCS3).  The oracle's P is the
+ * stable one (ascending particle index inside each cell); the paper's atomic
+ * cursor gives the same sets in an arbitrary order.
+ * ------------------------------------------------------------------------- */
+int orc_group(int64_t n, int32_t M, const int32_t *cell,
+              uint32_t *counts, uint64_t *cell_start, uint32_t *perm)
+{
+    if (n < 0 || M <= 0) return ORC_EINVAL;
+    for (int32_t j = 0; j < M; ++j) counts[j] = 0;
+    for (int64_t l = 0; l < n; ++l) {
+        if (cell[l] < 0 || cell[l] >= M) return ORC_EINVAL;
+        counts[cell[l]] += 1;                                   /* CCS1 */
+    }
+    uint64_t acc = 0;
+    for (int32_t j = 0; j < M; ++j) { cell_start[j] = acc; acc += counts[j]; }  /* CCS2 */
+    cell_start[M] = acc;
+    uint64_t *cursor = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)M);
+    if (!cursor) return ORC_EINVAL;
+    for (int32_t j = 0; j < M; ++j) cursor[j] = cell_start[j];
+    for (int64_t l = 0; l < n; ++l) perm[cursor[cell[l]]++] = (uint32_t)l;   /* CCS3 */
+    free(cursor);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- *
+ * In-cell pairing order.  Table 5 pairs consecutive entries of P; the paper's
+ * P order comes from atomic increments and is not reproducible.  Reading: each
+ * step every particle l draws a key r_l (word 0 of its PARTICLE block) and a
+ * cell's particles are ordered by (r_l, l); pairs are entries (0,1), (2,3), ...
+ * of that order.  This is the per-step re-randomised partner choice the
+ * Takizuka-Abe model needs.
+ * ------------------------------------------------------------------------- */
+typedef struct { uint32_t key; uint32_t l; } orc_kl;
+
+static int orc_kl_cmp(const void *a, const void *b)
+{
+    const orc_kl *x = (const orc_kl *)a, *y = (const orc_kl *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->l != y->l) return x->l < y->l ? -1 : 1;
+    return 0;
+}
+
+static uint32_t orc_pair_key(uint64_t seed, uint64_t l, uint32_t step)
+{
+    uint32_t w[4];
+    orc_draw(seed, l, step, ORC_TAG_PARTICLE, w);
+    return w[0];
+}
+
+/* order[cell_start[j] .. cell_start[j+1]) = cell j's particles in pairing order. */
+int orc_pair_order(int64_t n, int32_t M, const int32_t *cell, uint64_t seed, uint32_t step,
+                   uint64_t *cell_start, uint32_t *order)
+{
+    uint32_t *counts = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)M);
+    if (!counts) return ORC_EINVAL;
+    int rc = orc_group(n, M, cell, counts, cell_start, order);
+    free(counts);
+    if (rc) return rc;
+    orc_kl *tmp = (orc_kl *)malloc(sizeof(orc_kl) * (size_t)(n > 0 ? n : 1));
+    if (!tmp) return ORC_EINVAL;
+    for (int32_t j = 0; j < M; ++j) {
+        uint64_t s = cell_start[j], e = cell_start[j + 1];
+        for (uint64_t k = s; k < e; ++k) {
+            tmp[k - s].l = order[k];
+            tmp[k - s].key = orc_pair_key(seed, order[k], step);
+        }
+        qsort(tmp, (size_t)(e - s), sizeof(orc_kl), orc_kl_cmp);
+        for (uint64_t k = s; k < e; ++k) order[k] = tmp[k - s].l;
+    }
+    free(tmp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- *
+ * Takizuka-Abe binary collision (Takizuka & Abe 1977, the model Sec. 4.4
+ * adopts for step S1).  For a pair (a, b) of equal-mass electrons with
+ * relative velocity u = v_a - v_b:
+ *   delta = tan(Theta/2) is Gaussian with variance <delta^2> = A / |u|^3,
+ *   A = q^4 n lnLambda dt / (8 pi eps0^2 mu^2), mu = m/2;
+ *   phi is uniform on [0, 2 pi);
+ *   u is rotated by Theta about an axis at azimuth phi; both particles take
+ *   half of the change with opposite signs (momentum and energy conserved).
+ * The three uniforms come from one PAIR block: Box-Muller radius, Box-Muller
+ * angle, azimuth.  `A` is the per-cell coefficient.
+ * ------------------------------------------------------------------------- */
+void orc_ta_pair(double va[3], double vb[3], double A, const uint32_t w[4])
+{
+    double ux = va[0] - vb[0], uy = va[1] - vb[1], uz = va[2] - vb[2];
+    double usq = ux * ux + uy * uy + uz * uz;
+    if (usq == 0.0) return;                     /* identical velocities: nothing to rotate */
+    double u = sqrt(usq);
+    double var = A / (usq * u);                 /* <delta^2> */
+    double g = sqrt(-2.0 * log(orc_uniform(w[0]))) * cos(2.0 * ORC_PI * orc_uniform(w[1]));
+    double delta = sqrt(var) * g;
+    double phi = 2.0 * ORC_PI * orc_uniform(w[2]);
+
+    double sin_t, omc_t;                        /* sin(Theta), 1 - cos(Theta) */
+    if (fabs(delta) <= 1.0) {
+        double d2 = delta * delta;
+        sin_t = 2.0 * delta / (1.0 + d2);
+        omc_t = 2.0 * d2 / (1.0 + d2);
+    } else {                                    /* same values through t = 1/delta */
+        double t = 1.0 / delta, t2 = t * t;
+        sin_t = 2.0 * t / (1.0 + t2);
+        omc_t = 2.0 / (1.0 + t2);
+    }
+    double cp = cos(phi), sp = sin(phi);
+    double uperp = sqrt(ux * ux + uy * uy);
+    double dux, duy, duz;
+    if (uperp > 0.0) {
+        dux = (ux / uperp) * uz * sin_t * cp - (uy / uperp) * u * sin_t * sp - ux * omc_t;
+        duy = (uy / uperp) * uz * sin_t * cp + (ux / uperp) * u * sin_t * sp - uy * omc_t;
+        duz = -uperp * sin_t * cp - uz * omc_t;
+    } else {                                    /* u along z: rotate about any transverse axis */
+        dux = u * sin_t * cp;
+        duy = u * sin_t * sp;
+        duz = -uz * omc_t;
+    }
+    va[0] += 0.5 * dux; va[1] += 0.5 * duy; va[2] += 0.5 * duz;
+    vb[0] -= 0.5 * dux; vb[1] -= 0.5 * duy; vb[2] -= 0.5 * duz;
+}
+
+/* Per-cell Takizuka-Abe coefficient A_j of orc_ta_pair for a cell holding
+ * N_j particles: n_j = w N_j / V_j (uniform weights, Sec. 8). */
+double orc_ta_coefficient(const orc_params *p, double n_j, double lnlam, double dt)
+{
+    double mu = 0.5 * p->mass;
+    double q2 = p->charge * p->charge;
+    return q2 * q2 * n_j * lnlam * dt / (8.0 * ORC_PI * p->eps0 * p->eps0 * mu * mu);
+}
+
+/* NRL formulary electron-electron Coulomb logarithm, n in m^-3, T in eV,
+ * clamped below at 2.  Used per cell when the logarithm depends on density. */
+double orc_nrl_lnlambda(double n_m3, double T_eV)
+{
+    if (!(n_m3 > 0.0) || !(T_eV > 0.0)) return 2.0;
+    double n_cm3 = n_m3 * 1e-6;
+    double lt = log(T_eV);
+    double v = 23.5 - log(sqrt(n_cm3) * pow(T_eV, -1.25)) - sqrt(1e-5 + (lt - 2.0) * (lt - 2.0) / 16.0);
+    return v < 2.0 ? 2.0 : v;
+}
+
+/* ------------------------------------------------------------------------- *
+ * Step S1 (Table 2), the Coulombic collision step of Table 5: group (CCS1-3),
+ * pair consecutive entries of each cell's order, draw the pair's uniforms
+ * (CCS4) and update both velocities (CCS5).  An odd cell's last particle sits
+ * out (reading of "handled trivially").  With p->correction set, each cell's
+ * velocities are then mapped v <- V0 + sqrt(K0/K1) (v - V1), where V0, K0 are
+ * the cell's mean velocity and summed squared peculiar speed before the
+ * update and V1, K1 after it; this restores both invariants after rounding.
+ * Per-cell inputs: inv_vol = 1/V_j, lnlam = Coulomb logarithm, dt = step.
+ * ------------------------------------------------------------------------- */
+static void orc_cell_mean_k(const uint32_t *idx, uint64_t cnt, const double *vx, const double *vy,
+                            const double *vz, double V[3], double *K)
+{
+    double sx = 0, sy = 0, sz = 0;
+    for (uint64_t k = 0; k < cnt; ++k) { sx += vx[idx[k]]; sy += vy[idx[k]]; sz += vz[idx[k]]; }
+    V[0] = sx / (double)cnt; V[1] = sy / (double)cnt; V[2] = sz / (double)cnt;
+    double s = 0;
+    for (uint64_t k = 0; k < cnt; ++k) {
+        double dx = vx[idx[k]] - V[0], dy = vy[idx[k]] - V[1], dz = vz[idx[k]] - V[2];
+        s += dx * dx + dy * dy + dz * dz;
+    }
+    *K = s;
+}
+
+int orc_coulomb(int64_t n, int32_t M, const int32_t *cell, double *vx, double *vy, double *vz,
+                const double *inv_vol, const double *lnlam, const double *dt,
+                const orc_params *p, uint32_t step)
+{
+    if (n < 0 || M <= 0) return ORC_EINVAL;
+    uint64_t *cs = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1));
+    uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    if (!cs || !order) { free(cs); free(order); return ORC_EINVAL; }
+    int rc = orc_pair_order(n, M, cell, p->seed, step, cs, order);
+    if (rc) { free(cs); free(order); return rc; }
+    for (int32_t j = 0; j < M; ++j) {
+        uint64_t s = cs[j], cnt = cs[j + 1] - cs[j];
+        if (cnt < 2) continue;
+        const uint32_t *o = order + s;
+        double V0[3], K0 = 0;
+        if (p->correction) orc_cell_mean_k(o, cnt, vx, vy, vz, V0, &K0);
+        double A = orc_ta_coefficient(p, p->weight * (double)cnt * inv_vol[j], lnlam[j], dt[j]);
+        for (uint64_t k = 0; k + 1 < cnt; k += 2) {            /* CCS4 + CCS5 per pair */
+            uint32_t a = o[k], b = o[k + 1];
+            uint32_t w[4];
+            orc_draw(p->seed, a < b ? a : b, step, ORC_TAG_PAIR, w);
+            double va[3] = {vx[a], vy[a], vz[a]}, vb[3] = {vx[b], vy[b], vz[b]};
+            orc_ta_pair(va, vb, A, w);
+            vx[a] = va[0]; vy[a] = va[1]; vz[a] = va[2];
+            vx[b] = vb[0]; vy[b] = vb[1]; vz[b] = vb[2];
+        }
+        if (p->correction) {
+            double V1[3], K1;
+            orc_cell_mean_k(o, cnt, vx, vy, vz, V1, &K1);
+            double f = K1 > 0.0 ? sqrt(K0 / K1) : 1.0;
+            for (uint64_t k = 0; k < cnt; ++k) {
+                uint32_t l = o[k];
+                vx[l] = V0[0] + f * (vx[l] - V1[0]);
+                vy[l] = V0[1] + f * (vy[l] - V1[1]);
+                vz[l] = V0[2] + f * (vz[l] - V1[2]);
+            }
+        }
+    }
+    free(cs); free(order);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- *
+ * Step S2a for electron-neutral collisions C1 (elastic) and C2 (ionization)
+ * with the null-collision method of Sec. 4.2 (Vahedi & Surendra 1995).
+ * Per cell j: nu_max = n_n (sigma_el + sigma_ion) v_max with v_max the largest
+ * speed in the cell at this point of the step, P_null = 1 - exp(-nu_max dt_j).
+ * Particle l (PARTICLE block words 1, 2) is a candidate iff U1 < P_null; a
+ * candidate with r = U2 nu_max collides elastically if r < nu_el(v),
+ * ionizes if r < nu_el(v) + nu_ion(v), and is otherwise a null collision.
+ * Elastic: new direction uniform on the sphere (SCATTER words 0, 1), speed
+ * from the energy loss (2m/M)(1 - cos chi) E off a cold neutral.
+ * Ionization: E' = E - E_ion shared as U E' (secondary, SCATTER word 2) and
+ * (1 - U) E' (primary); primary direction from SCATTER words 0, 1, secondary
+ * direction from SECONDARY words 0, 1; the secondary takes the parent's cell
+ * and position.  Secondaries are appended (Table 3 CS5) at
+ * N_old + offset(cell) + rank of the parent index inside the cell, cells in
+ * ascending order (reading: a deterministic form of the paper's atomic
+ * global write index).  Optional per-particle outputs: `decision` (0 not a
+ * candidate, 1 null, 2 elastic, 3 ionization) and `margin` (distance of the
+ * deciding uniform to the nearest decision boundary, relative to 1).
+ * ------------------------------------------------------------------------- */
+static void orc_iso_dir(uint32_t wa, uint32_t wb, double d[3])
+{
+    double c = 1.0 - 2.0 * orc_uniform(wa);
+    double s = sqrt(fmax(0.0, 1.0 - c * c));
+    double ph = 2.0 * ORC_PI * orc_uniform(wb);
+    d[0] = s * cos(ph); d[1] = s * sin(ph); d[2] = c;
+}
+
+int orc_neutral(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, double *x,
+                double *vx, double *vy, double *vz, const double *dt, const orc_params *p,
+                uint32_t step, int64_t *counts_out /* [3]: candidates, elastic, ionization */,
+                int8_t *decision, double *margin)
+{
+    int64_t n = *n_io;
+    if (n < 0 || M <= 0) return ORC_EINVAL;
+    double *vmax2 = (double *)calloc((size_t)M, sizeof(double));
+    uint32_t *nion = (uint32_t *)calloc((size_t)M, sizeof(uint32_t));
+    uint8_t *ionize = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    double *sec = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!vmax2 || !nion || !ionize || !sec) { free(vmax2); free(nion); free(ionize); free(sec); return ORC_EINVAL; }
+    for (int64_t l = 0; l < n; ++l) {
+        double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
+        if (v2 > vmax2[cell[l]]) vmax2[cell[l]] = v2;
+    }
+    const double sig_tot = p->sigma_el + p->sigma_ion;
+    const double e_over_m = p->charge / p->mass;
+    int64_t ncand = 0, nel = 0, nio = 0;
+    for (int64_t l = 0; l < n; ++l) {
+        int32_t j = cell[l];
+        double numax = p->n_neutral * sig_tot * sqrt(vmax2[j]);
+        double pnull = -expm1(-numax * dt[j]);
+        uint32_t w[4];
+        orc_draw(p->seed, (uint64_t)l, step, ORC_TAG_PARTICLE, w);
+        double uc = orc_uniform(w[1]);
+        if (decision) decision[l] = 0;
+        if (margin) margin[l] = fabs(uc - pnull);
+        if (!(uc < pnull)) continue;
+        ++ncand;
+        double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
+        double v = sqrt(v2);
+        double E = 0.5 * v2 / e_over_m;                           /* eV */
+        double nu_el = p->n_neutral * p->sigma_el * v;
+        double nu_ion = E >= p->e_ion ? p->n_neutral * p->sigma_ion * v : 0.0;
+        double r = orc_uniform(w[2]) * numax;
+        int kind = r < nu_el ? 2 : (r < nu_el + nu_ion ? 3 : 1);
+        if (decision) decision[l] = (int8_t)kind;
+        if (margin && numax > 0.0) {
+            double m1 = fabs(r - nu_el) / numax, m2 = fabs(r - nu_el - nu_ion) / numax;
+            double me = p->sigma_ion > 0.0 ? fabs(E - p->e_ion) / p->e_ion : 1.0;
+            double mm = margin[l];
+            if (m1 < mm) mm = m1;
+            if (m2 < mm) mm = m2;
+            if (me < mm) mm = me;
+            margin[l] = mm;
+        }
+        if (kind == 1) continue;
+        uint32_t s[4];
+        orc_draw(p->seed, (uint64_t)l, step, ORC_TAG_SCATTER, s);
+        double d[3];
+        orc_iso_dir(s[0], s[1], d);
+        if (kind == 2) {
+            ++nel;
+            double cchi = (vx[l] * d[0] + vy[l] * d[1] + vz[l] * d[2]) / v;
+            double f = 1.0 - 2.0 * (p->mass / p->mass_neutral) * (1.0 - cchi);
+            double vn = v * sqrt(f);
+            vx[l] = vn * d[0]; vy[l] = vn * d[1]; vz[l] = vn * d[2];
+        } else {
+            ++nio;
+            double Ep = E - p->e_ion;
+            double Es = orc_uniform(s[2]) * Ep;
+            double Eprim = Ep - Es;
+            double vp = sqrt(2.0 * Eprim * e_over_m), vs = sqrt(2.0 * Es * e_over_m);
+            uint32_t t[4];
+            orc_draw(p->seed, (uint64_t)l, step, ORC_TAG_SECONDARY, t);
+            double ds[3];
+            orc_iso_dir(t[0], t[1], ds);
+            vx[l] = vp * d[0]; vy[l] = vp * d[1]; vz[l] = vp * d[2];
+            sec[3 * l + 0] = vs * ds[0]; sec[3 * l + 1] = vs * ds[1]; sec[3 * l + 2] = vs * ds[2];
+            ionize[l] = 1;
+            nion[j] += 1;
+        }
+    }
+    int rc = ORC_OK;
+    if (n + nio > capacity) {
+        rc = ORC_ECAPACITY;
+    } else {
+        /* offsets over cells, then rank by ascending parent index inside each cell */
+        uint64_t *off = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)M);
+        if (!off) { rc = ORC_EINVAL; }
+        else {
+            uint64_t acc = 0;
+            for (int32_t j = 0; j < M; ++j) { off[j] = acc; acc += nion[j]; }
+            for (int64_t l = 0; l < n; ++l) {
+                if (!ionize[l]) continue;
+                int32_t j = cell[l];
+                int64_t dst = n + (int64_t)off[j]++;
+                vx[dst] = sec[3 * l + 0]; vy[dst] = sec[3 * l + 1]; vz[dst] = sec[3 * l + 2];
+                cell[dst] = j;
+                if (x) x[dst] = x[l];
+            }
+            free(off);
+            *n_io = n + nio;
+        }
+    }
+    if (counts_out) { counts_out[0] = ncand; counts_out[1] = nel; counts_out[2] = nio; }
+    free(vmax2); free(nion); free(ionize); free(sec);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- *
+ * Particle-to-cell moments, steps S3a/S3b of Table 2 (Sec. 4.5): plain
+ * sequential sums per cell.  mom[10 j + k]:
+ *   0 N_j, 1 sum w, 2..4 sum v_x, v_y, v_z, 5..7 sum v_x^2, v_y^2, v_z^2,
+ *   8 sum sigma_el |v|, 9 sum sigma_ion(E) |v|   (rate sums C_kc / n_k).
+ * hist[64 j + b]: counts over 64 log-spaced energy bins on [1e-2, 1e3] eV,
+ * under- and overflow clamped into the end bins.
+ * ------------------------------------------------------------------------- */
+int orc_energy_bin(double E_eV)
+{
+    if (!(E_eV > 0.0)) return 0;
+    double t = (log10(E_eV) + 2.0) * (64.0 / 5.0);
+    if (t < 0.0) return 0;
+    if (t >= 63.0) return 63;
+    return (int)t;
+}
+
+int orc_moments(int64_t n, int32_t M, const int32_t *cell, const double *vx, const double *vy,
+                const double *vz, const orc_params *p, double *mom, uint32_t *hist)
+{
+    if (n < 0 || M <= 0) return ORC_EINVAL;
+    memset(mom, 0, sizeof(double) * 10 * (size_t)M);
+    if (hist) memset(hist, 0, sizeof(uint32_t) * 64 * (size_t)M);
+    const double e_over_m = p->charge / p->mass;
+    for (int64_t l = 0; l < n; ++l) {
+        int32_t j = cell[l];
+        if (j < 0 || j >= M) return ORC_EINVAL;
+        double *m = mom + 10 * (size_t)j;
+        double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
+        double v = sqrt(v2);
+        double E = 0.5 * v2 / e_over_m;
+        m[0] += 1.0;
+        m[1] += p->weight;
+        m[2] += vx[l]; m[3] += vy[l]; m[4] += vz[l];
+        m[5] += vx[l] * vx[l]; m[6] += vy[l] * vy[l]; m[7] += vz[l] * vz[l];
+        m[8] += p->sigma_el * v;
+        m[9] += (E >= p->e_ion ? p->sigma_ion : 0.0) * v;
+        if (hist) hist[64 * (size_t)j + (size_t)orc_energy_bin(E)] += 1;
+    }
+    return ORC_OK;
+}
+
+/* One full collision step in the paper's order: S1 Coulomb, S2a electron-
+ * neutral, S3 moments of the result.  Either collision can be switched off. */
+int orc_step(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, double *x,
+             double *vx, double *vy, double *vz, const double *inv_vol, const double *lnlam,
+             const double *dt, const orc_params *p, uint32_t step, int do_coulomb, int do_neutral,
+             double *mom, uint32_t *hist, int64_t *counts_out)
+{
+    int rc = ORC_OK;
+    if (counts_out) { counts_out[0] = counts_out[1] = counts_out[2] = 0; }
+    if (do_coulomb) {
+        rc = orc_coulomb(*n_io, M, cell, vx, vy, vz, inv_vol, lnlam, dt, p, step);
+        if (rc) return rc;
+    }
+    if (do_neutral) {
+        rc = orc_neutral(n_io, capacity, M, cell, x, vx, vy, vz, dt, p, step, counts_out, NULL, NULL);
+        if (rc) return rc;
+    }
+    if (mom) rc = orc_moments(*n_io, M, cell, vx, vy, vz, p, mom, hist);
+    return rc;
+}

@@ -1,0 +1,226 @@
+"""Pins for the oracle's Takizuka-Abe Coulomb step (CPU only).
+
+Checked against what the mathematics and the paper fix: rotation invariants
+and conservation of each binary collision, the Gaussian law of tan(Theta/2),
+uniform azimuths, brute-force composition on tiny cells, exact per-cell
+conservation over many steps, a Maxwellian staying stationary, and the
+anisotropic relaxation rate of the NRL formulary.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+from paper_2508_06771_gb300 import workloads as W
+
+
+def _words(orc, n, seed=99):
+    return [orc.draw(seed, i, 3, orc.TAG_PAIR) for i in range(n)]
+
+
+def test_ta_pair_invariants(orc):
+    rng = np.random.default_rng(1)
+    for i, w in enumerate(_words(orc, 400)):
+        va = rng.standard_normal(3) * 1e6
+        vb = rng.standard_normal(3) * 1e6
+        A = 10 ** rng.uniform(10, 20)  # spans small and large deflections
+        na, nb = orc.ta_pair(va, vb, A, w)
+        u, up = va - vb, na - nb
+        assert np.allclose(na + nb, va + vb, rtol=0, atol=1e-9 * np.abs(va).max())
+        assert math.isclose(np.dot(up, up), np.dot(u, u), rel_tol=1e-14)
+        assert math.isclose(np.dot(na, na) + np.dot(nb, nb), np.dot(va, va) + np.dot(vb, vb), rel_tol=1e-14)
+
+
+def test_ta_deflection_statistics(orc):
+    # <tan^2(Theta/2)> = <delta^2> = A/u^3 and azimuth phi uniform about u.
+    u_vec = np.array([3.0e5, -1.0e5, 2.0e5])
+    u = np.linalg.norm(u_vec)
+    var = 0.02
+    A = var * u ** 3
+    e1 = np.cross(u_vec, [0, 0, 1.0]); e1 /= np.linalg.norm(e1)
+    e2 = np.cross(u_vec / u, e1)
+    t2, phis = [], []
+    for w in _words(orc, 20000, seed=5):
+        na, nb = orc.ta_pair(u_vec, np.zeros(3), A, w)
+        up = na - nb
+        c = np.dot(up, u_vec) / u ** 2
+        t2.append((1 - c) / (1 + c))
+        perp = up - np.dot(up, u_vec) / u ** 2 * u_vec
+        phis.append(math.atan2(np.dot(perp, e2), np.dot(perp, e1)))
+    t2 = np.array(t2)
+    se = math.sqrt(2.0 / t2.size) * var
+    assert abs(t2.mean() - var) < 5 * se
+    h, _ = np.histogram(phis, bins=24, range=(-math.pi, math.pi))
+    assert stats.chisquare(h).pvalue > 1e-4
+
+
+def test_ta_parallel_and_zero_relative(orc):
+    w = orc.draw(1, 2, 3, orc.TAG_PAIR)
+    va = np.array([0.0, 0.0, 5e5]); vb = np.array([0.0, 0.0, -5e5])
+    na, nb = orc.ta_pair(va, vb, 1e18, w)
+    assert math.isclose(np.linalg.norm(na - nb), 1e6, rel_tol=1e-14)
+    assert np.allclose(na + nb, 0, atol=1e-8)
+    same = np.array([1e5, 2e5, 3e5])
+    na, nb = orc.ta_pair(same, same.copy(), 1e18, w)
+    assert np.array_equal(na, same) and np.array_equal(nb, same)
+
+
+def test_coulomb_tiny_cells_brute_force(orc):
+    wl = W.ragged(M=8, mean_ppc=2, seed=3)
+    counts = np.array([0, 1, 2, 3, 4, 5, 2, 3])
+    n = int(counts.sum())
+    rng = np.random.default_rng(4)
+    cell = np.repeat(np.arange(8, dtype=np.int32), counts)
+    wl.update(M=8, vx=rng.standard_normal(n) * 4e5, vy=rng.standard_normal(n) * 4e5,
+              vz=rng.standard_normal(n) * 4e5, cell=cell, inv_vol=np.full(8, 1e18),
+              dt_cell=np.full(8, 3e-9), lnlam_cell=np.full(8, 10.0), capacity=n)
+    P = orc.make_params(wl)
+    st = orc.State(wl)
+    step = 17
+    orc.coulomb(st, P, step)
+    cs, order = orc.pair_order(cell, 8, wl["seed"], step)
+    vx0, vy0, vz0 = wl["vx"], wl["vy"], wl["vz"]
+    for j in range(8):
+        o = [int(t) for t in order[cs[j]:cs[j + 1]]]
+        N = len(o)
+        A = orc.ta_coefficient(P, wl["weight"] * N * 1e18, 10.0, 3e-9)
+        for k in range(0, N - 1, 2):
+            a, b = o[k], o[k + 1]
+            w = orc.draw(wl["seed"], min(a, b), step, orc.TAG_PAIR)
+            na, nb = orc.ta_pair([vx0[a], vy0[a], vz0[a]], [vx0[b], vy0[b], vz0[b]], A, w)
+            assert np.array_equal([st.vx[a], st.vy[a], st.vz[a]], na)
+            assert np.array_equal([st.vx[b], st.vy[b], st.vz[b]], nb)
+        if N % 2:
+            l = o[-1]
+            assert (st.vx[l], st.vy[l], st.vz[l]) == (vx0[l], vy0[l], vz0[l])
+
+
+def _cell_invariants(st, M):
+    vx, vy, vz, cell = st.views()
+    P = np.stack([np.bincount(cell, weights=c, minlength=M) for c in (vx, vy, vz)], 1)
+    E = np.bincount(cell, weights=vx * vx + vy * vy + vz * vz, minlength=M)
+    return P, E
+
+
+def _temps(st, mass, charge):
+    vx, vy, vz, _ = st.views()
+    return [mass * (v.var()) / charge for v in (vx, vy, vz)]
+
+
+def test_coulomb_conservation_100_steps(orc):
+    wl = W.cfg1(M=8, ppc=1000)
+    P = orc.make_params(wl)
+    st = orc.State(wl)
+    p0, e0 = _cell_invariants(st, wl["M"])
+    for s in range(100):
+        orc.coulomb(st, P, s)
+    p1, e1 = _cell_invariants(st, wl["M"])
+    vth = math.sqrt(e0.mean() / 1000)
+    assert np.abs(p1 - p0).max() / (1000 * vth) < 1e-12
+    assert (np.abs(e1 - e0) / e0).max() < 1e-12
+    assert np.array_equal(np.bincount(st.views()[3], minlength=8), np.full(8, 1000))
+
+
+def test_correction_restores_invariants(orc):
+    # Perturb velocities after a step: the correction must map back to V0, K0 exactly.
+    wl = W.ragged(M=5, mean_ppc=40, seed=21, with_empty=False)
+    P = orc.make_params(wl, correction=True)
+    st = orc.State(wl)
+    p0, e0 = _cell_invariants(st, wl["M"])
+    for s in range(20):
+        orc.coulomb(st, P, s)
+    p1, e1 = _cell_invariants(st, wl["M"])
+    assert np.allclose(p1, p0, rtol=0, atol=1e-9 * np.sqrt(e0.max()))
+    assert np.allclose(e1, e0, rtol=1e-13)
+
+
+def test_maxwellian_stationary(orc):
+    wl = W.cfg1(M=16, ppc=1000)
+    rng = np.random.default_rng(8)
+    vt = math.sqrt(2.0 * W.E_CHARGE / W.M_E)
+    for k in ("vx", "vy", "vz"):
+        wl[k] = rng.standard_normal(wl["vx"].size) * vt
+    P = orc.make_params(wl)
+    st = orc.State(wl)
+    for s in range(100):
+        orc.coulomb(st, P, s)
+    vx, vy, vz, _ = st.views()
+    T = _temps(st, W.M_E, W.E_CHARGE)
+    n = vx.size
+    sigT = 2.0 * math.sqrt(2.0 / n)
+    assert max(T) - min(T) < 3 * math.sqrt(2) * sigT
+    for v in (vx, vy, vz):
+        assert stats.kstest(v / vt, "norm").pvalue > 0.01
+
+
+def nrl_isotropization_rate(Tpar, Tperp, n, lnlam):
+    """NRL formulary temperature-isotropization rate nu_T for like particles (SI)."""
+    e2 = W.E_CHARGE ** 2 / (4 * math.pi * W.EPS0)
+    A = Tperp / Tpar - 1.0
+    kTpar = Tpar * W.E_CHARGE
+    pref = 2 * math.sqrt(math.pi) * e2 ** 2 * n * lnlam / (math.sqrt(W.M_E) * kTpar ** 1.5)
+    if abs(A) < 1e-3:
+        # series of A^-2 [-3 + (A+3) g(A)] about A = 0 (both branches share it)
+        f = 4.0 / 15.0 - 8.0 * A / 35.0 + 4.0 * A * A / 21.0
+    elif A < 0:
+        s = math.sqrt(-A)
+        f = (-3 + (A + 3) * math.atanh(s) / s) / A ** 2
+    else:
+        s = math.sqrt(A)
+        f = (-3 + (A + 3) * math.atan(s) / s) / A ** 2
+    return pref * f
+
+
+def relaxation_reference(Tpar0, Tperp0, n, lnlam, times):
+    def rhs(t, y):
+        tpar, tperp = y
+        nu = nrl_isotropization_rate(tpar, tperp, n, lnlam)
+        return [2 * nu * (tperp - tpar), -nu * (tperp - tpar)]
+    sol = integrate.solve_ivp(rhs, (0, times[-1]), [Tpar0, Tperp0], t_eval=times, rtol=1e-10, atol=1e-14,
+                              method="DOP853", max_step=(times[1] - times[0]))
+    return sol.y
+
+
+def test_nrl_rate_at_cfg1_start():
+    # Closed-form value quoted for the 2 eV / 1 eV, 1e18 m^-3, lnL = 10 case.
+    assert math.isclose(nrl_isotropization_rate(2.0, 1.0, 1e18, 10.0), 5.06e6, rel_tol=2e-3)
+
+
+def _relaxation_rate_ratio(orc, div, M=256, t_end=53e-9, seed=0):
+    """Fitted e-folding rate of T_par - T_perp over [0, t_end] divided by the NRL ODE's, at
+    dt = tau_e / div (tau_e = 1/nu_e of the cfg1 plasma)."""
+    wl = W.cfg1(M=M, seed=seed)
+    dt = wl["dt"] * 10.0 / div
+    wl["dt_cell"] = np.full(M, dt)
+    P = orc.make_params(wl)
+    st = orc.State(wl)
+    steps = int(round(t_end / dt))
+    dT = []
+    for s in range(steps + 1):
+        vx, vy, vz, _ = st.views()
+        dT.append(W.M_E * (np.mean(vz * vz) - 0.5 * np.mean(vx * vx + vy * vy)) / W.E_CHARGE)
+        if s < steps:
+            orc.coulomb(st, P, s)
+    t = np.arange(steps + 1) * dt
+    ref_par, ref_perp = relaxation_reference(2.0, 1.0, wl["density"], 10.0, t)
+    k = -np.polyfit(t, np.log(dT), 1)[0]
+    k_ref = -np.polyfit(t, np.log(ref_par - ref_perp), 1)[0]
+    return k / k_ref
+
+
+def test_anisotropic_relaxation_rate(orc):
+    """Relaxation of T_par - T_perp against the NRL isotropization ODE.
+
+    Takizuka-Abe with a finite step under-relaxes: pairs slow enough that <delta^2> > 1 saturate
+    at large angles, which removes a share of the rate that scales like (nu_e dt)^(1/3).  The rate
+    is measured at dt = tau_e/10 (the cfg1 step), tau_e/20 and tau_e/40, extrapolated linearly in
+    dt^(1/3) to dt -> 0, and that limit must equal the NRL rate.  A factor-2 error in the
+    deflection variance would put the limit near 2."""
+    divs = np.array([10.0, 20.0, 40.0])
+    r = np.array([_relaxation_rate_ratio(orc, d) for d in divs])
+    assert np.all(np.diff(r) > 0), r                  # converges from below as dt shrinks
+    x = (1.0 / divs) ** (1.0 / 3.0)
+    slope, r0 = np.polyfit(x, r, 1)
+    assert abs(r0 - 1.0) < 0.08, (r, r0)
+    assert 0.6 < r[0] < 0.9, r                        # the cfg1 step's known deficit
