@@ -314,9 +314,10 @@ int orc_coulomb(int64_t n, int32_t M, const int32_t *cell, double *vx, double *v
  * (1 - U) E' (primary); primary direction from SCATTER words 0, 1, secondary
  * direction from SECONDARY words 0, 1; the secondary takes the parent's cell
  * and position.  Secondaries are appended (Table 3 CS5) at
- * N_old + offset(cell) + rank of the parent index inside the cell, cells in
- * ascending order (reading: a deterministic form of the paper's atomic
- * global write index).  Optional per-particle outputs: `decision` (0 not a
+ * N_old + offset(cell) + rank of the parent inside the cell, cells in
+ * ascending order and parents in the cell's pairing order of this step
+ * (sorted by (PARTICLE word 0, index)); reading: a deterministic form of the
+ * paper's atomic global write index.  Optional outputs: `decision` (0 not a
  * candidate, 1 null, 2 elastic, 3 ionization) and `margin` (distance of the
  * deciding uniform to the nearest decision boundary, relative to 1).
  * ------------------------------------------------------------------------- */
@@ -406,23 +407,24 @@ int orc_neutral(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, doubl
     if (n + nio > capacity) {
         rc = ORC_ECAPACITY;
     } else {
-        /* offsets over cells, then rank by ascending parent index inside each cell */
-        uint64_t *off = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)M);
-        if (!off) { rc = ORC_EINVAL; }
-        else {
-            uint64_t acc = 0;
-            for (int32_t j = 0; j < M; ++j) { off[j] = acc; acc += nion[j]; }
-            for (int64_t l = 0; l < n; ++l) {
+        /* cells in ascending order; inside a cell, parents in pairing order */
+        uint64_t *cs = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1));
+        uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+        if (!cs || !order || orc_pair_order(n, M, cell, p->seed, step, cs, order) != ORC_OK) {
+            rc = ORC_EINVAL;
+        } else {
+            int64_t dst = n;
+            for (int64_t k = 0; k < n; ++k) {
+                uint32_t l = order[k];
                 if (!ionize[l]) continue;
-                int32_t j = cell[l];
-                int64_t dst = n + (int64_t)off[j]++;
                 vx[dst] = sec[3 * l + 0]; vy[dst] = sec[3 * l + 1]; vz[dst] = sec[3 * l + 2];
-                cell[dst] = j;
+                cell[dst] = cell[l];
                 if (x) x[dst] = x[l];
+                ++dst;
             }
-            free(off);
             *n_io = n + nio;
         }
+        free(cs); free(order);
     }
     if (counts_out) { counts_out[0] = ncand; counts_out[1] = nel; counts_out[2] = nio; }
     free(vmax2); free(nion); free(ionize); free(sec);

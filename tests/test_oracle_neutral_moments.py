@@ -96,7 +96,7 @@ def test_elastic_energy_loss_and_bookkeeping(orc):
     assert math.isclose(total_after, expect, rel_tol=1e-12)
 
 
-def test_secondaries_appended_in_cell_then_parent_order(orc):
+def test_secondaries_appended_in_cell_then_pairing_order(orc):
     M, n = 5, 20_000
     wl = _maxwell_cell(n, 30.0, seed=8, M=M)
     # interleave cells so parent order differs from cell order
@@ -112,7 +112,8 @@ def test_secondaries_appended_in_cell_then_parent_order(orc):
     N0 = n * M
     parents = np.where(out["decision"] == 3)[0]
     cells = wl["cell"][parents]
-    want = parents[np.lexsort((parents, cells))]
+    keys = np.array([orc.draw(wl["seed"], int(l), 1, orc.TAG_PARTICLE)[0] for l in parents], np.uint64)
+    want = parents[np.lexsort((parents, keys, cells))]   # cell, then (pairing key, index)
     assert st.n == N0 + parents.size
     assert np.array_equal(st.cell[N0:st.n], wl["cell"][want])
     assert np.array_equal(st.x[N0:st.n], wl["x"][want])
