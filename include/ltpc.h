@@ -1,0 +1,178 @@
+/*
+ * ltpc.h -- C ABI of the GB300 collision core for collisional-plasma PIC
+ * (Almgren-Bell, Al Awar, Geethakrishnan, Gligoric, Biros, "A Portable
+ * Multi-GPU Solver for Collisional Plasmas with Coulombic Interactions",
+ * arXiv 2508.06771).
+ *
+ * The library implements, on one GPU, the particle side of one PIC step of
+ * Table 2 of the paper:
+ *   S1   electron-electron Coulomb collisions, Takizuka-Abe binary model over
+ *        a per-cell random pairing (Sec. 4.4, Table 5, CCS1-CCS5);
+ *   S2a  electron-neutral elastic (C1) and ionization (C2) collisions with the
+ *        null-collision method (Sec. 4.2, Table 3);
+ *   S3   per-cell moments (particle-to-cell, Sec. 4.5).
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (LTPC_OK) on success or a negative LTPC_E* code.  No C++
+ *     exception or abort crosses the ABI.
+ *   - Work is enqueued asynchronously on the CUDA stream given at creation.
+ *     Errors detected on the device are sticky and returned by the next
+ *     ltpc_sync (or by any call documented as synchronizing).
+ *   - The library allocates no device memory: the caller passes two device
+ *     buffers sized by ltpc_required_bytes and keeps ownership of them.
+ *   - Device arrays are structure-of-arrays, element type given by
+ *     ltpc_config.precision (float for LTPC_F32, double for LTPC_F64).
+ *   - Particle ids are storage indices 0..n-1.  Random numbers are a pure
+ *     function of (seed, particle id or pair id, step, use): Philox4x32-10.
+ */
+#ifndef LTPC_H
+#define LTPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LTPC_OK 0
+#define LTPC_EINVAL (-1)       /* bad argument or configuration            */
+#define LTPC_ECAPACITY (-2)    /* ionization would exceed the capacity     */
+#define LTPC_ECUDA (-3)        /* a CUDA runtime call failed               */
+#define LTPC_ETIMEOUT (-4)     /* a bounded device-side wait gave up       */
+#define LTPC_ENONFINITE (-5)   /* a loaded velocity is NaN or infinite     */
+#define LTPC_EUNSUPPORTED (-6) /* a cell is larger than the largest class  */
+#define LTPC_EINTERNAL (-7)    /* an internal bounds check failed          */
+
+#define LTPC_F32 0
+#define LTPC_F64 1
+
+#define LTPC_LNL_CONST 0       /* Coulomb logarithm per cell from lnlambda[] */
+#define LTPC_LNL_NRL 1         /* NRL e-e formula from the cell's moments    */
+
+typedef struct ltpc_ctx ltpc_ctx; /* opaque, host-side, owned by the library */
+
+/* Species, grid and run parameters (SI units; energies in eV).
+ * Cell j holds electrons of density n_j = weight * N_j * inv_volume[j] and
+ * advances with time step dt_j = dt * dt_factor[j].  Host arrays are copied
+ * by ltpc_create and may be freed afterwards. */
+typedef struct ltpc_config {
+    int32_t precision;          /* LTPC_F32 or LTPC_F64                        */
+    int32_t n_cells;            /* M >= 1 (all plasma instances together)      */
+    int64_t capacity;           /* N_max: particle slots (Sec. 4.1 buffers)    */
+    uint64_t seed;              /* Philox key                                  */
+    double mass;                /* electron mass m [kg]                        */
+    double charge;              /* elementary charge e [C]                     */
+    double eps0;                /* vacuum permittivity [F/m]                   */
+    double weight;              /* macro-particle weight w (uniform)           */
+    double n_neutral;           /* neutral density n_n [1/m^3]; 0: no S2a      */
+    double mass_neutral;        /* neutral mass M [kg]                         */
+    double sigma_el;            /* constant elastic cross section [m^2]        */
+    double sigma_ion;           /* ionization cross section above threshold    */
+    double e_ion;               /* ionization threshold [eV]                   */
+    int32_t lnlambda_mode;      /* LTPC_LNL_CONST or LTPC_LNL_NRL              */
+    int32_t correction;         /* -1 default (on for F32, off for F64), 0, 1  */
+    int32_t has_position;       /* 1: keep a position array x (copied to
+                                   secondaries); 0: no positions              */
+    int32_t use_graph;          /* 1: ltpc_step/ltpc_run replay a CUDA graph   */
+    const double* inv_volume;   /* host [M]: 1/V_j                             */
+    const double* dt_factor;    /* host [M] or NULL (all 1)                    */
+    const double* lnlambda;     /* host [M] or NULL (all 10); constant mode    */
+    int32_t reserved[8];        /* must be zero                                */
+} ltpc_config;
+
+/* Bytes of the two caller-owned device buffers for `cfg`.
+ * state_bytes: particle arrays (vx, vy, vz, cell, optional x) for
+ *              cfg->capacity particles.  work_bytes: grouping, staging,
+ *              moments and per-cell tables.  Pure host computation. */
+int ltpc_required_bytes(const ltpc_config* cfg, size_t* state_bytes, size_t* work_bytes);
+
+/* Create a context on the current CUDA device.  d_state / d_work: device
+ * buffers of at least the sizes above, 256-byte aligned, owned by the caller
+ * and valid until ltpc_destroy.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream).  Synchronizing.  Errors: EINVAL (bad config/pointers),
+ * ECUDA. */
+int ltpc_create(ltpc_ctx** out, const ltpc_config* cfg, void* d_state, void* d_work, void* cuda_stream);
+
+/* Release host-side resources (graphs, the context).  The caller frees the
+ * device buffers.  NULL is ignored. */
+void ltpc_destroy(ltpc_ctx* ctx);
+
+/* Load n particles: cell ids (int32, in [0, M)), optional positions x (only
+ * if has_position, else ignored), velocities vx, vy, vz in the context's
+ * precision.  src_is_device selects host or device sources.  Builds the
+ * per-cell grouping (CCS1-CCS3) and the moments of the loaded state.
+ * Synchronizing.  Errors: EINVAL (n < 0 or n > capacity), ENONFINITE,
+ * EINVAL for cell ids out of range (reported by this call), ECUDA. */
+int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const void* x,
+                        const void* vx, const void* vy, const void* vz, int src_is_device);
+
+/* Step S1 only: Takizuka-Abe Coulomb collisions (Sec. 4.4) with time step
+ * dt (cell j uses dt * dt_factor[j]) at step number `step` (0 <= step <
+ * 2^32), then the moments.  Asynchronous. */
+int ltpc_collide_coulomb(ltpc_ctx* ctx, double dt, int64_t step);
+
+/* Step S2a only: null-collision electron-neutral elastic and ionization
+ * collisions (Sec. 4.2); secondaries are appended (the particle count may
+ * grow), then the moments.  Asynchronous; ECAPACITY is reported by
+ * ltpc_sync when the capacity would be exceeded (the secondaries of that
+ * pass are dropped and the primaries keep their post-collision state). */
+int ltpc_collide_neutral(ltpc_ctx* ctx, double dt, int64_t step);
+
+/* One full collision step S1 + S2a + S3 (S2a only when n_neutral > 0), fused
+ * in one pass per cell.  With use_graph the pass is captured once as a CUDA
+ * graph and replayed.  Asynchronous. */
+int ltpc_step(ltpc_ctx* ctx, double dt, int64_t step);
+
+/* nsteps consecutive ltpc_step calls for steps step0, step0+1, ... */
+int ltpc_run(ltpc_ctx* ctx, double dt, int64_t step0, int64_t nsteps);
+
+/* Per-cell moments of the last pass: mom[10 j + k] (double) with k =
+ * 0 N_j, 1 w N_j, 2-4 sum v_x, v_y, v_z, 5-7 sum v_x^2, v_y^2, v_z^2,
+ * 8 sum sigma_el |v|, 9 sum sigma_ion(E) |v|; hist[64 j + b] (uint32):
+ * counts in 64 log-spaced energy bins on [1e-2, 1e3] eV (end bins clamp).
+ * Either pointer may be NULL.  Host destinations synchronize the stream. */
+int ltpc_moments(ltpc_ctx* ctx, double* mom, uint32_t* hist, int dst_is_device);
+
+/* Copy the particles out: velocities, cell ids, optional positions (any
+ * pointer may be NULL); *n_out receives the particle count.  Synchronizing. */
+int ltpc_read_particles(ltpc_ctx* ctx, void* vx, void* vy, void* vz, int32_t* cell, void* x,
+                        int64_t* n_out, int dst_is_device);
+
+/* Wait for all work and return (then clear) deferred device errors. */
+int ltpc_sync(ltpc_ctx* ctx);
+
+/* Inspection: the pairing order of step `step` for the current grouping
+ * (Table 5 pairs entries 2k, 2k+1 of each cell's segment) written to device
+ * arrays order[n] and cell_start[M+1] (uint32).  Leaves the particles
+ * unchanged.  Asynchronous. */
+int ltpc_pair_order(ltpc_ctx* ctx, int64_t step, uint32_t* d_order, uint32_t* d_cell_start);
+
+/* Inspection: the grouping of CCS1-CCS3 (cell_start[M+1], perm[n], counts[M];
+ * device pointers, any may be NULL).  Asynchronous. */
+int ltpc_grouping(ltpc_ctx* ctx, uint32_t* d_cell_start, uint32_t* d_perm, uint32_t* d_counts);
+
+/* Cluster classes used for cells of different sizes: class i handles cells
+ * with max_n[i-1] < N_j <= max_n[i].  ltpc_classes reports the active ones
+ * (cluster size, threads per CTA, positions per CTA, largest cell). */
+int ltpc_classes(ltpc_ctx* ctx, int32_t* n_classes, int32_t* cluster, int32_t* threads,
+                 int32_t* per_cta, int32_t* max_n);
+
+/* Choose among the compiled class tables by timing one pass of each on the
+ * loaded particles (particles are restored afterwards).  The choice changes
+ * only the schedule; the per-cell arithmetic may round differently between
+ * tables (reductions follow the CTA shape).  Synchronizing. */
+int ltpc_autotune(ltpc_ctx* ctx, double dt, int32_t* chosen_table);
+int ltpc_set_class_table(ltpc_ctx* ctx, int32_t table);
+
+/* Short text for a status code (static storage). */
+const char* ltpc_strerror(int code);
+
+/* Last CUDA error text recorded by the context ("" if none). */
+const char* ltpc_last_cuda_error(ltpc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LTPC_H */

@@ -1,0 +1,23 @@
+// k_cells_f32.cu -- float instantiations of the cell kernel (velocities and the
+// collision arithmetic in binary32; per-cell sums combined in double).
+#include "k_cells_inst.cuh"
+
+namespace ltpc {
+
+static const CellKernelEntry kF32[] = {
+    CellKernel<float, 1, 256, 8>::entry(),    // 0: cells <= 2048
+    CellKernel<float, 2, 256, 8>::entry(),    // 1: <= 4096
+    CellKernel<float, 4, 256, 12>::entry(),   // 2: <= 12288
+    CellKernel<float, 8, 256, 16>::entry(),   // 3: <= 32768
+    CellKernel<float, 8, 512, 16>::entry(),   // 4: <= 65536
+    CellKernel<float, 1, 512, 8>::entry(),    // 5: <= 4096
+    CellKernel<float, 1, 1024, 12>::entry(),  // 6: <= 12288, one CTA per cell
+};
+
+int cell_kernels_f32(const CellKernelEntry** out)
+{
+    *out = kF32;
+    return (int)(sizeof(kF32) / sizeof(kF32[0]));
+}
+
+}  // namespace ltpc

@@ -1,0 +1,66 @@
+// k_cells_inst.cuh -- launch wrapper for one compiled shape of the cell kernel.
+#pragma once
+#include "k_cells.cuh"
+#include "ltpc_launch.h"
+
+namespace ltpc {
+
+template <class T, int C, int NT, int ITEMS>
+struct CellKernel {
+    static constexpr uint32_t capl = (uint32_t)NT * ITEMS;
+    static size_t smem() { return cells_dyn_smem<T>(capl); }
+    static cudaLaunchConfig_t config(cudaLaunchAttribute* attr, int grid, cudaStream_t st)
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid, 1, 1);
+        cfg.blockDim = dim3(NT, 1, 1);
+        cfg.dynamicSmemBytes = smem();
+        cfg.stream = st;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cfg;
+    }
+    static cudaError_t prepare()
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_cells<T, C, NT, ITEMS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        return e;
+    }
+    static cudaError_t occupancy(int* clusters)
+    {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = config(attr, C, 0);
+        return cudaOccupancyMaxActiveClusters(clusters, k_cells<T, C, NT, ITEMS>, &cfg);
+    }
+    static cudaError_t launch(const CellArgs<T>& a, cudaStream_t st, int grid_ctas)
+    {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        if (grid_ctas <= 0) {
+            int cl = 0;
+            e = occupancy(&cl);
+            if (e != cudaSuccess) return e;
+            grid_ctas = (cl > 0 ? cl : 1) * C;
+        }
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = config(attr, grid_ctas, st);
+        return cudaLaunchKernelEx(&cfg, k_cells<T, C, NT, ITEMS>, a);
+    }
+    static CellKernelEntry entry()
+    {
+        CellKernelEntry k;
+        k.shape = CellShape{C, NT, ITEMS};
+        k.launcher = (void*)&launch;
+        k.occupancy = &occupancy;
+        k.smem_bytes = smem();
+        return k;
+    }
+};
+
+}  // namespace ltpc

@@ -1,0 +1,304 @@
+// k_group.cu -- per-cell grouping of particle ids (Table 5, CCS1-CCS3) and the
+// bookkeeping between passes: append of ionization secondaries (Table 3, CS5),
+// new cell offsets, and the cluster-class work lists of the cell kernel.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ltpc_internal.h"
+#include "ltpc_launch.h"
+
+namespace ltpc {
+
+// CCS1 at load time: N_j by warp-aggregated atomics (counts must be zero).
+static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __restrict__ counts, int32_t M,
+                       DevState* ds)
+{
+    const unsigned long long n = ds->n;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += stride) {
+        const int32_t c = cell[l];
+        const unsigned act = __activemask();
+        if (c < 0 || c >= M) {
+            atomicOr(&ds->err, ERR_BAD_CELL);
+            continue;
+        }
+        const unsigned peers = __match_any_sync(act, c);
+        const unsigned leader = __ffs(peers) - 1;
+        if ((threadIdx.x & 31u) == leader) atomicAdd(&counts[c], (uint32_t)__popc(peers));
+    }
+}
+
+// CCS3: perm[I_j + rank] = l with one atomic cursor update per warp and cell.
+static __global__ void k_scatter(const int32_t* __restrict__ cell, uint32_t* __restrict__ cursor,
+                          uint32_t* __restrict__ perm, const DevState* __restrict__ ds)
+{
+    const unsigned long long n = ds->n;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned lane = threadIdx.x & 31u;
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += stride) {
+        const int32_t c = cell[l];
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, c);
+        const unsigned leader = __ffs(peers) - 1;
+        uint32_t base = 0u;
+        if (lane == leader) base = atomicAdd(&cursor[c], (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        perm[base + rank] = (uint32_t)l;
+    }
+}
+
+// Single-CTA bookkeeping between passes (REGROUP_THREADS threads):
+//   1. if `append`: exclusive scan of this pass's secondaries per cell into
+//      ion_off, capacity check, counts += ion_count, keep the old offsets;
+//   2. CCS2: cell_start = exclusive scan of counts, cursor = cell_start;
+//   3. cluster-class work lists (cells in ascending index order per class);
+//   4. reset the work tickets, optionally advance the step number.
+static __global__ void __launch_bounds__(REGROUP_THREADS)
+k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_start,
+          uint32_t* __restrict__ cs_prev, uint32_t* __restrict__ cursor,
+          uint32_t* __restrict__ ion_count, uint32_t* __restrict__ ion_off, RegroupLists lists,
+          unsigned long long capacity, int append, int advance_step, DevState* ds)
+{
+    constexpr int NT = REGROUP_THREADS;
+    __shared__ uint32_t s_w[NT / 32 + 1];
+    __shared__ uint32_t s_cls[MAX_CLASSES][NT / 32 + 1];
+    __shared__ unsigned long long s_total;
+    __shared__ uint32_t s_max;
+    const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    if (tid == 0) s_max = 0u;
+    const uint32_t per = (uint32_t)((M + NT - 1) / NT);
+    const uint32_t b0 = min((uint32_t)M, tid * per), b1 = min((uint32_t)M, b0 + per);
+
+    auto block_scan = [&](uint32_t v, uint32_t* tot) -> uint32_t {
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        if (lane == 31u) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t wv = lane < NT / 32 ? s_w[lane] : 0u;
+            uint32_t z = wv;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+                if (lane >= (unsigned)o) z += y;
+            }
+            if (lane < NT / 32) s_w[lane] = z - wv;
+            if (lane == NT / 32 - 1) s_w[NT / 32] = z;
+        }
+        __syncthreads();
+        const uint32_t r = s_w[warp] + x - v;
+        *tot = s_w[NT / 32];
+        __syncthreads();
+        return r;
+    };
+
+    // 1. secondaries of the last pass
+    uint32_t total_ion = 0u;
+    bool appended = false;
+    if (append) {
+        uint32_t sum = 0u;
+        for (uint32_t c = b0; c < b1; ++c) sum += ion_count[c];
+        uint32_t tot;
+        uint32_t ex = block_scan(sum, &tot);
+        if (tid == 0) s_total = (unsigned long long)tot;
+        __syncthreads();
+        const unsigned long long n0 = ds->n;
+        appended = tot > 0u && n0 + tot <= capacity;
+        if (tot > 0u && !appended && tid == 0) atomicOr(&ds->err, ERR_CAPACITY);
+        for (uint32_t c = b0; c < b1; ++c) {
+            ion_off[c] = ex;
+            ex += ion_count[c];
+            cs_prev[c] = cell_start[c];
+            if (appended) counts[c] += ion_count[c];
+            ion_count[c] = 0u;
+        }
+        if (tid == 0) { ion_off[M] = tot; cs_prev[M] = cell_start[M]; }
+        total_ion = appended ? tot : 0u;
+        __syncthreads();
+    }
+
+    // 2. CCS2: offsets of the grouping
+    {
+        uint32_t sum = 0u;
+        for (uint32_t c = b0; c < b1; ++c) sum += counts[c];
+        uint32_t tot;
+        uint32_t ex = block_scan(sum, &tot);
+        for (uint32_t c = b0; c < b1; ++c) {
+            cell_start[c] = ex;
+            cursor[c] = ex;
+            ex += counts[c];
+        }
+        if (tid == 0) cell_start[M] = tot;
+    }
+
+    // 3. work lists: class of a cell = first class whose max_n covers it
+    {
+        uint32_t cnt[MAX_CLASSES];
+        for (int k = 0; k < MAX_CLASSES; ++k) cnt[k] = 0u;
+        uint32_t mx = 0u;
+        for (uint32_t c = b0; c < b1; ++c) {
+            const uint32_t n = counts[c];
+            mx = max(mx, n);
+            if (n == 0u) continue;
+            int k = 0;
+            while (k < lists.n_classes - 1 && n > lists.max_n[k]) ++k;
+            ++cnt[k];
+        }
+        for (int k = 0; k < lists.n_classes; ++k) {
+            uint32_t x = cnt[k];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= (unsigned)o) x += y;
+            }
+            if (lane == 31u) s_cls[k][warp] = x;
+            cnt[k] = x - cnt[k];   // exclusive within the warp
+        }
+        // reduce the largest count
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+        __syncthreads();
+        if (warp == 0) {
+            for (int k = 0; k < lists.n_classes; ++k) {
+                const uint32_t wv = lane < NT / 32 ? s_cls[k][lane] : 0u;
+                uint32_t z = wv;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+                    if (lane >= (unsigned)o) z += y;
+                }
+                if (lane < NT / 32) s_cls[k][lane] = z - wv;
+                if (lane == NT / 32 - 1) s_cls[k][NT / 32] = z;
+            }
+        }
+        if (lane == 0) atomicMax(&s_max, mx);
+        __syncthreads();
+        uint32_t pos[MAX_CLASSES];
+        for (int k = 0; k < lists.n_classes; ++k) pos[k] = s_cls[k][warp] + cnt[k];
+        for (uint32_t c = b0; c < b1; ++c) {
+            const uint32_t n = counts[c];
+            if (n == 0u) continue;
+            int k = 0;
+            while (k < lists.n_classes - 1 && n > lists.max_n[k]) ++k;
+            if (n > lists.max_n[k]) atomicOr(&ds->err, ERR_CELL_TOO_LARGE);
+            lists.list[k][pos[k]++] = c;
+        }
+        if (tid < (unsigned)MAX_CLASSES) {
+            ds->class_n[tid] = tid < (unsigned)lists.n_classes ? s_cls[tid][NT / 32] : 0u;
+            ds->ticket[tid] = 0u;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        ds->max_count = s_max;
+        ds->n_ion = total_ion;
+        ds->n += total_ion;
+        if (advance_step) ds->step += 1u;
+    }
+}
+
+// Copy the secondaries staged by the last pass to the end of the particle
+// arrays: secondary g (in cell order, then pairing-order position of the
+// parent) goes to slot n_old + g with the parent's cell and position.
+template <class T>
+static __global__ void k_append(int32_t M, const uint32_t* __restrict__ ion_off, const uint32_t* __restrict__ cs_prev,
+                         const uint32_t* __restrict__ stage_l, const T* __restrict__ svx,
+                         const T* __restrict__ svy, const T* __restrict__ svz, T* __restrict__ vx,
+                         T* __restrict__ vy, T* __restrict__ vz, int32_t* __restrict__ cell,
+                         T* __restrict__ x, const DevState* __restrict__ ds)
+{
+    const uint32_t tot = ds->n_ion;
+    if (tot == 0u) return;
+    const unsigned long long n0 = ds->n - tot;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < tot; g += gridDim.x * blockDim.x) {
+        // last cell j with ion_off[j] <= g
+        int32_t lo = 0, hi = M - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (ion_off[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t src = cs_prev[lo] + (g - ion_off[lo]);
+        const unsigned long long dst = n0 + g;
+        const uint32_t parent = stage_l[src];
+        vx[dst] = svx[src]; vy[dst] = svy[src]; vz[dst] = svz[src];
+        cell[dst] = lo;
+        if (x) x[dst] = x[parent];
+    }
+}
+
+static __global__ void k_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step)
+{
+    if (set_n) { ds->n = n; ds->n_ion = 0u; }
+    if (set_step) { ds->step = step; ds->dt = dt; }
+}
+
+// Load-time validation: non-finite velocities.
+template <class T>
+static __global__ void k_check_finite(const T* __restrict__ vx, const T* __restrict__ vy, const T* __restrict__ vz,
+                               DevState* ds)
+{
+    const unsigned long long n = ds->n;
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+         l += (unsigned long long)gridDim.x * blockDim.x) {
+        if (!isfinite(vx[l]) || !isfinite(vy[l]) || !isfinite(vz[l])) {
+            atomicOr(&ds->err, ERR_NONFINITE);
+            return;
+        }
+    }
+}
+cudaError_t launch_hist(const int32_t* cell, uint32_t* counts, int32_t M, DevState* ds, int grid, cudaStream_t s)
+{
+    k_hist<<<grid, 256, 0, s>>>(cell, counts, M, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const int32_t* cell, uint32_t* cursor, uint32_t* perm, const DevState* ds, int grid,
+                           cudaStream_t s)
+{
+    k_scatter<<<grid, 256, 0, s>>>(cell, cursor, perm, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regroup(int32_t M, uint32_t* counts, uint32_t* cell_start, uint32_t* cs_prev, uint32_t* cursor,
+                           uint32_t* ion_count, uint32_t* ion_off, const RegroupLists& lists,
+                           unsigned long long capacity, int append, int advance_step, DevState* ds, cudaStream_t s)
+{
+    k_regroup<<<1, REGROUP_THREADS, 0, s>>>(M, counts, cell_start, cs_prev, cursor, ion_count, ion_off, lists,
+                                            capacity, append, advance_step, ds);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_append(int32_t M, const uint32_t* ion_off, const uint32_t* cs_prev, const uint32_t* stage_l,
+                          const T* svx, const T* svy, const T* svz, T* vx, T* vy, T* vz, int32_t* cell, T* x,
+                          const DevState* ds, int grid, cudaStream_t s)
+{
+    k_append<T><<<grid, 256, 0, s>>>(M, ion_off, cs_prev, stage_l, svx, svy, svz, vx, vy, vz, cell, x, ds);
+    return cudaGetLastError();
+}
+template cudaError_t launch_append<float>(int32_t, const uint32_t*, const uint32_t*, const uint32_t*, const float*,
+                                          const float*, const float*, float*, float*, float*, int32_t*, float*,
+                                          const DevState*, int, cudaStream_t);
+template cudaError_t launch_append<double>(int32_t, const uint32_t*, const uint32_t*, const uint32_t*,
+                                           const double*, const double*, const double*, double*, double*, double*,
+                                           int32_t*, double*, const DevState*, int, cudaStream_t);
+
+cudaError_t launch_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step,
+                             cudaStream_t s)
+{
+    k_set_state<<<1, 1, 0, s>>>(ds, n, set_n, step, dt, set_step);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_check_finite(const T* vx, const T* vy, const T* vz, DevState* ds, int grid, cudaStream_t s)
+{
+    k_check_finite<T><<<grid, 256, 0, s>>>(vx, vy, vz, ds);
+    return cudaGetLastError();
+}
+template cudaError_t launch_check_finite<float>(const float*, const float*, const float*, DevState*, int,
+                                                cudaStream_t);
+template cudaError_t launch_check_finite<double>(const double*, const double*, const double*, DevState*, int,
+                                                 cudaStream_t);
+
+}  // namespace ltpc

@@ -1,0 +1,69 @@
+// ltpc_internal.h -- structures shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ltpc {
+
+// Device-detected error bits (reported by ltpc_sync as LTPC_E* codes).
+enum : uint32_t {
+    ERR_CAPACITY = 1u,       // appended secondaries would exceed the capacity
+    ERR_TIMEOUT = 2u,        // a bounded device-side wait gave up
+    ERR_NONFINITE = 4u,      // a loaded velocity is not finite
+    ERR_INDEX = 8u,          // an internal index failed its bounds check (bug guard)
+    ERR_CELL_TOO_LARGE = 16u,// a cell exceeds the largest cluster class
+    ERR_BAD_CELL = 32u,      // a loaded cell id is outside [0, M)
+};
+
+// What one pass of the cell kernel does.
+enum : uint32_t {
+    F_COULOMB = 1u,          // step S1: Takizuka-Abe pair collisions
+    F_NEUTRAL = 2u,          // step S2a: electron-neutral null-collision sampling
+    F_CORRECTION = 4u,       // restore per-cell momentum and energy after S1
+    F_LNL_NRL = 8u,          // Coulomb logarithm from the cell's previous moments
+};
+
+constexpr int MAX_CLASSES = 8;
+constexpr int NMOM = 10;     // moments per cell
+constexpr int NBIN = 64;     // energy-histogram bins per cell
+
+// Small device-resident state.  Step number and dt live here so that a
+// captured CUDA graph can be replayed for any step.
+struct DevState {
+    unsigned long long n;             // particles currently stored
+    unsigned int err;                 // ERR_* bits, sticky until read
+    unsigned int step;                // step number used by the next pass
+    double dt;                        // base time step (cell dt = dt * dt_factor[j])
+    unsigned int class_n[MAX_CLASSES];// cells in each cluster-class work list
+    unsigned int ticket[MAX_CLASSES]; // dynamic work counters, reset every step
+    unsigned int n_ion;               // secondaries appended by the last pass
+    unsigned int max_count;           // largest cell at the last regrouping
+};
+
+// Arguments of the cell kernel (one cluster per cell).
+template <class T>
+struct CellArgs {
+    T* vx; T* vy; T* vz;
+    const uint32_t* perm;        // particle ids grouped by cell (CCS3 output)
+    const uint32_t* counts;      // N_j
+    const uint32_t* cell_start;  // I_j
+    const double* inv_vol;       // 1 / V_j
+    const double* dt_factor;     // per-cell multiplier of dt
+    const double* lnlam;         // constant Coulomb logarithm per cell
+    double* mom;                 // [M][NMOM]
+    uint32_t* hist;              // [M][NBIN]
+    uint32_t* ion_count;         // [M] secondaries staged by this pass
+    uint32_t* stage_l;           // parent id of each staged secondary
+    T* stage_vx; T* stage_vy; T* stage_vz;
+    DevState* ds;
+    const uint32_t* list;        // cells of this class
+    uint32_t cls;
+    uint32_t flags;
+    uint64_t seed;
+    double coef0;                // q^4 w / (8 pi eps0^2 mu^2), mu = m/2
+    double weight, mass, e_over_m;
+    double n_neutral, sigma_el, sigma_ion, e_ion, mratio2;  // mratio2 = 2 m / M
+    uint32_t* order_out;         // optional: pairing order written at I_j + position
+};
+
+}  // namespace ltpc

@@ -1,0 +1,69 @@
+// philox.cuh -- counter-based random numbers for the collision kernels.
+//
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplies with the published multipliers, the key advanced
+// by the published Weyl increments after every round.  Streams are addressed
+// by counter (id, step, tag, 0) under key = seed, so every draw is a pure
+// function of (seed, particle or pair id, step, use) and no random-number
+// array is stored (the paper precomputes such arrays with cupy, Sec. 4.2 and
+// Sec. 4.4).
+#pragma once
+#include <stdint.h>
+
+namespace ltpc {
+
+enum : uint32_t { TAG_PARTICLE = 1u, TAG_PAIR = 2u, TAG_SCATTER = 3u, TAG_SECONDARY = 4u };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Block for stream `tag` of id `id` (particle index, or the smaller index of a
+// pair) at step `step`.
+__device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t id, uint32_t step, uint32_t tag)
+{
+    return philox4x32_10(id, step, tag, 0u, k0, k1);
+}
+
+// Uniform variates on (0, 1].  Double: (w + 1/2) 2^-32, exact, in (0, 1).
+// Float: ((w >> 8) + 1) 2^-24, exact in binary32, in (0, 1].
+template <class T> __device__ __forceinline__ T unif(uint32_t w);
+template <> __device__ __forceinline__ double unif<double>(uint32_t w)
+{
+    return fma((double)w, 0x1p-32, 0x1p-33);
+}
+template <> __device__ __forceinline__ float unif<float>(uint32_t w)
+{
+    return __uint2float_rn((w >> 8) + 1u) * 0x1p-24f;
+}
+
+// Range of unif(w) over all w sharing the top 16 bits `hi` (used to decide
+// the null-collision candidate test without redrawing the stream).
+template <class T> __device__ __forceinline__ void unif_hi16_range(uint32_t hi, T& lo, T& up);
+template <> __device__ __forceinline__ void unif_hi16_range<double>(uint32_t hi, double& lo, double& up)
+{
+    lo = fma((double)(hi << 16), 0x1p-32, 0x1p-33);
+    up = fma((double)((hi << 16) | 0xFFFFu), 0x1p-32, 0x1p-33);
+}
+template <> __device__ __forceinline__ void unif_hi16_range<float>(uint32_t hi, float& lo, float& up)
+{
+    lo = __uint2float_rn((hi << 8) + 1u) * 0x1p-24f;
+    up = __uint2float_rn((hi << 8) + 256u) * 0x1p-24f;
+}
+
+}  // namespace ltpc

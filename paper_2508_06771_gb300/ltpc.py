@@ -1,0 +1,307 @@
+"""Thin ctypes binding of the C ABI in ``include/ltpc.h``.
+
+Argument marshalling only: every step of the collision path runs in the CUDA
+library ``_lib/libltpc.so``.  PyTorch provides the device buffers and the
+stream.  There is no CPU fallback: importing works without a GPU, but creating
+a ``Collider`` needs the library and a CUDA device and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libltpc.so")
+
+OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EINTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
+F32, F64 = 0, 1
+LNL_CONST, LNL_NRL = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LtpcError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: {strerror(code) if _lib else code} ({code})"
+        if detail:
+            msg += f" [{detail}]"
+        super().__init__(msg)
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("n_cells", C.c_int32), ("capacity", C.c_int64), ("seed", C.c_uint64),
+        ("mass", C.c_double), ("charge", C.c_double), ("eps0", C.c_double), ("weight", C.c_double),
+        ("n_neutral", C.c_double), ("mass_neutral", C.c_double), ("sigma_el", C.c_double),
+        ("sigma_ion", C.c_double), ("e_ion", C.c_double),
+        ("lnlambda_mode", C.c_int32), ("correction", C.c_int32), ("has_position", C.c_int32),
+        ("use_graph", C.c_int32),
+        ("inv_volume", C.POINTER(C.c_double)), ("dt_factor", C.POINTER(C.c_double)),
+        ("lnlambda", C.POINTER(C.c_double)), ("reserved", C.c_int32 * 8),
+    ]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libltpc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FileNotFoundError(f"{path} not built; run paper_2508_06771_gb300/build.py")
+        L = C.CDLL(path)
+        vp, i32, i64, u32p, f64p = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_uint32), C.POINTER(C.c_double)
+        cfgp = C.POINTER(Config)
+        sig = {
+            "ltpc_required_bytes": (C.c_int, [cfgp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+            "ltpc_create": (C.c_int, [C.POINTER(vp), cfgp, vp, vp, vp]),
+            "ltpc_destroy": (None, [vp]),
+            "ltpc_load_particles": (C.c_int, [vp, i64, vp, vp, vp, vp, vp, C.c_int]),
+            "ltpc_collide_coulomb": (C.c_int, [vp, C.c_double, i64]),
+            "ltpc_collide_neutral": (C.c_int, [vp, C.c_double, i64]),
+            "ltpc_step": (C.c_int, [vp, C.c_double, i64]),
+            "ltpc_run": (C.c_int, [vp, C.c_double, i64, i64]),
+            "ltpc_moments": (C.c_int, [vp, vp, vp, C.c_int]),
+            "ltpc_read_particles": (C.c_int, [vp, vp, vp, vp, vp, vp, C.POINTER(i64), C.c_int]),
+            "ltpc_sync": (C.c_int, [vp]),
+            "ltpc_pair_order": (C.c_int, [vp, i64, vp, vp]),
+            "ltpc_grouping": (C.c_int, [vp, vp, vp, vp]),
+            "ltpc_classes": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(i32)]),
+            "ltpc_autotune": (C.c_int, [vp, C.c_double, C.POINTER(i32)]),
+            "ltpc_set_class_table": (C.c_int, [vp, i32]),
+            "ltpc_strerror": (C.c_char_p, [C.c_int]),
+            "ltpc_last_cuda_error": (C.c_char_p, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def strerror(code: int) -> str:
+    return load_library().ltpc_strerror(code).decode()
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _f64p(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Collider:
+    """One collision context on the current CUDA device (see include/ltpc.h)."""
+
+    def __init__(self, *, n_cells: int, capacity: int, inv_volume, precision: int = F32, seed: int = 0,
+                 mass: float, charge: float, eps0: float, weight: float = 1.0, n_neutral: float = 0.0,
+                 mass_neutral: float = 1.0, sigma_el: float = 0.0, sigma_ion: float = 0.0, e_ion: float = 1e30,
+                 lnlambda_mode: int = LNL_CONST, correction: int = -1, has_position: bool = False,
+                 use_graph: bool = True, dt_factor=None, lnlambda=None, device=None, stream=None):
+        import torch
+
+        self.torch = torch
+        self.L = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("ltpc needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.precision = precision
+        self.dtype = torch.float32 if precision == F32 else torch.float64
+        self.np_dtype = np.float32 if precision == F32 else np.float64
+        self.M = int(n_cells)
+        self.capacity = int(capacity)
+        self._inv = np.ascontiguousarray(inv_volume, dtype=np.float64)
+        self._dtf = None if dt_factor is None else np.ascontiguousarray(dt_factor, dtype=np.float64)
+        self._lnl = None if lnlambda is None else np.ascontiguousarray(lnlambda, dtype=np.float64)
+        cfg = Config()
+        cfg.precision, cfg.n_cells, cfg.capacity, cfg.seed = precision, self.M, self.capacity, int(seed)
+        cfg.mass, cfg.charge, cfg.eps0, cfg.weight = mass, charge, eps0, weight
+        cfg.n_neutral, cfg.mass_neutral, cfg.sigma_el, cfg.sigma_ion, cfg.e_ion = (
+            n_neutral, mass_neutral, sigma_el, sigma_ion, e_ion)
+        cfg.lnlambda_mode, cfg.correction = lnlambda_mode, correction
+        cfg.has_position, cfg.use_graph = int(bool(has_position)), int(bool(use_graph))
+        cfg.inv_volume = _f64p(self._inv)
+        cfg.dt_factor = _f64p(self._dtf) if self._dtf is not None else None
+        cfg.lnlambda = _f64p(self._lnl) if self._lnl is not None else None
+        self.cfg = cfg
+        sb, wb = C.c_size_t(), C.c_size_t()
+        self._check(self.L.ltpc_required_bytes(C.byref(cfg), C.byref(sb), C.byref(wb)), "required_bytes")
+        self.state_bytes, self.work_bytes = sb.value, wb.value
+        with torch.cuda.device(self.device):
+            self.d_state = torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
+            self.d_work = torch.empty(self.work_bytes, dtype=torch.uint8, device=self.device)
+        ctx = C.c_void_p()
+        rc = self.L.ltpc_create(C.byref(ctx), C.byref(cfg), _ptr(self.d_state), _ptr(self.d_work),
+                                self.stream.cuda_stream)
+        self._check(rc, "create")
+        self.ctx = ctx
+
+    @classmethod
+    def from_workload(cls, wl: dict, precision: int | None = None, correction: int = -1, use_graph=True,
+                      capacity: int | None = None, **kw):
+        prec = precision if precision is not None else (F32 if wl.get("precision") == "f32" else F64)
+        dt = float(np.max(wl["dt_cell"]))
+        c = cls(n_cells=wl["M"], capacity=int(capacity or wl["capacity"]), inv_volume=wl["inv_vol"],
+                precision=prec, seed=wl["seed"], mass=wl["mass"], charge=wl["charge"], eps0=wl["eps0"],
+                weight=wl["weight"], n_neutral=wl["n_neutral"] if wl.get("neutral", True) else 0.0,
+                mass_neutral=wl["mass_neutral"], sigma_el=wl["sigma_el"], sigma_ion=wl["sigma_ion"],
+                e_ion=wl["e_ion"], lnlambda_mode=wl.get("lnlam_mode", 0), correction=correction,
+                has_position=wl.get("x") is not None, use_graph=use_graph,
+                dt_factor=np.asarray(wl["dt_cell"]) / dt, lnlambda=wl["lnlam_cell"], **kw)
+        c.dt = dt
+        return c
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, rc, where):
+        if rc != OK:
+            detail = ""
+            if rc == ECUDA and getattr(self, "ctx", None):
+                detail = self.L.ltpc_last_cuda_error(self.ctx).decode()
+            raise LtpcError(rc, where, detail)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.L.ltpc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a, dtype):
+        t = self.torch
+        if isinstance(a, t.Tensor):
+            return a.to(device=self.device, dtype=dtype).contiguous()
+        return t.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=self.device)
+
+    # ------------------------------------------------------------------ API
+    def load(self, vx, vy, vz, cell, x=None):
+        """Load particles from numpy arrays or tensors (copied to the device first)."""
+        t = self.torch
+        n = int(len(cell))
+        vxd, vyd, vzd = (self._dev(v, self.dtype) for v in (vx, vy, vz))
+        cd = self._dev(cell, t.int32)
+        xd = self._dev(x, self.dtype) if x is not None else None
+        self._check(self.L.ltpc_load_particles(self.ctx, n, _ptr(cd), _ptr(xd), _ptr(vxd), _ptr(vyd), _ptr(vzd), 1),
+                    "load_particles")
+        self._keep = (vxd, vyd, vzd, cd, xd)
+        return self
+
+    def load_host(self, vx, vy, vz, cell, x=None):
+        """Load from host arrays (numpy, pinned tensors) through the C ABI's host path."""
+        arrs = [np.ascontiguousarray(v, dtype=self.np_dtype) for v in (vx, vy, vz)]
+        c = np.ascontiguousarray(cell, dtype=np.int32)
+        xa = np.ascontiguousarray(x, dtype=self.np_dtype) if x is not None else None
+        p = lambda a: a.ctypes.data if a is not None else None
+        self._check(self.L.ltpc_load_particles(self.ctx, c.size, p(c), p(xa), p(arrs[0]), p(arrs[1]), p(arrs[2]), 0),
+                    "load_particles")
+        return self
+
+    def load_workload(self, wl):
+        return self.load(wl["vx"], wl["vy"], wl["vz"], wl["cell"], wl.get("x"))
+
+    def collide_coulomb(self, dt, step):
+        self._check(self.L.ltpc_collide_coulomb(self.ctx, float(dt), int(step)), "collide_coulomb")
+
+    def collide_neutral(self, dt, step):
+        self._check(self.L.ltpc_collide_neutral(self.ctx, float(dt), int(step)), "collide_neutral")
+
+    def step(self, dt, step):
+        self._check(self.L.ltpc_step(self.ctx, float(dt), int(step)), "step")
+
+    def run(self, dt, step0, nsteps):
+        self._check(self.L.ltpc_run(self.ctx, float(dt), int(step0), int(nsteps)), "run")
+
+    def sync(self):
+        self._check(self.L.ltpc_sync(self.ctx), "sync")
+
+    def sync_code(self) -> int:
+        return int(self.L.ltpc_sync(self.ctx))
+
+    def moments(self, as_numpy=True):
+        t = self.torch
+        mom = t.empty((self.M, 10), dtype=t.float64, device=self.device)
+        hist = t.empty((self.M, 64), dtype=t.int32, device=self.device)
+        self._check(self.L.ltpc_moments(self.ctx, _ptr(mom), _ptr(hist), 1), "moments")
+        if as_numpy:
+            self.stream.synchronize()
+            return mom.cpu().numpy(), hist.cpu().numpy().view(np.uint32)
+        return mom, hist
+
+    def moments_host(self, mom: np.ndarray, hist: np.ndarray | None = None):
+        """Moments straight into host arrays (synchronizing)."""
+        self._check(self.L.ltpc_moments(self.ctx, mom.ctypes.data, hist.ctypes.data if hist is not None else None, 0),
+                    "moments")
+
+    def count(self) -> int:
+        n = C.c_int64()
+        self._check(self.L.ltpc_read_particles(self.ctx, None, None, None, None, None, C.byref(n), 1), "count")
+        return n.value
+
+    def read(self):
+        """(vx, vy, vz, cell, x) as numpy arrays of the current particles."""
+        t = self.torch
+        n = self.count()
+        vx, vy, vz = (t.empty(max(n, 1), dtype=self.dtype, device=self.device) for _ in range(3))
+        cell = t.empty(max(n, 1), dtype=t.int32, device=self.device)
+        x = t.empty(max(n, 1), dtype=self.dtype, device=self.device) if self.cfg.has_position else None
+        nn = C.c_int64()
+        self._check(self.L.ltpc_read_particles(self.ctx, _ptr(vx), _ptr(vy), _ptr(vz), _ptr(cell), _ptr(x),
+                                               C.byref(nn), 1), "read_particles")
+        out = [a[:n].cpu().numpy() for a in (vx, vy, vz, cell)]
+        out.append(x[:n].cpu().numpy() if x is not None else None)
+        return tuple(out)
+
+    def pair_order(self, step):
+        t = self.torch
+        n = self.count()
+        order = t.zeros(max(n, 1), dtype=t.int32, device=self.device)
+        cs = t.zeros(self.M + 1, dtype=t.int32, device=self.device)
+        self._check(self.L.ltpc_pair_order(self.ctx, int(step), _ptr(order), _ptr(cs)), "pair_order")
+        self.sync()
+        return cs.cpu().numpy().view(np.uint32), order[:n].cpu().numpy().view(np.uint32)
+
+    def grouping(self):
+        t = self.torch
+        n = self.count()
+        perm = t.zeros(max(n, 1), dtype=t.int32, device=self.device)
+        cs = t.zeros(self.M + 1, dtype=t.int32, device=self.device)
+        counts = t.zeros(self.M, dtype=t.int32, device=self.device)
+        self._check(self.L.ltpc_grouping(self.ctx, _ptr(cs), _ptr(perm), _ptr(counts)), "grouping")
+        self.sync()
+        return (cs.cpu().numpy().view(np.uint32), perm[:n].cpu().numpy().view(np.uint32),
+                counts.cpu().numpy().view(np.uint32))
+
+    def classes(self):
+        n = C.c_int32()
+        arrs = [(C.c_int32 * 8)() for _ in range(4)]
+        self._check(self.L.ltpc_classes(self.ctx, C.byref(n), *arrs), "classes")
+        return [dict(cluster=arrs[0][k], threads=arrs[1][k], per_cta=arrs[2][k], max_n=arrs[3][k])
+                for k in range(n.value)]
+
+    def set_class_table(self, table: int):
+        self._check(self.L.ltpc_set_class_table(self.ctx, int(table)), "set_class_table")
+
+    def autotune(self, dt=0.0) -> int:
+        ch = C.c_int32()
+        self._check(self.L.ltpc_autotune(self.ctx, float(dt), C.byref(ch)), "autotune")
+        return ch.value
+
+
+def header_symbols(header: str | None = None):
+    """Function names declared in include/ltpc.h."""
+    import re
+    header = header or os.path.join(os.path.dirname(_HERE), "include", "ltpc.h")
+    txt = open(header).read()
+    return sorted(set(re.findall(r"\b(ltpc_[a-z0-9_]+)\s*\(", txt)))

@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: grouping and pairing order bit-exact; FP64 velocities within 1e-12
+relative per particle; FP32 per-cell moments within 1e-5 (see _fp32_bar).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_06771_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_06771_gb300 import build as B
+    from paper_2508_06771_gb300 import ltpc
+    B.build()
+    ltpc.load_library()
+    return ltpc
+
+
+def big_cells_workload(counts, seed=3, T_eV=2.0, shuffled=True, dens=1e18):
+    """Cells with the given counts (spanning every cluster class), optionally shuffled storage."""
+    counts = np.asarray(counts, np.int64)
+    M = counts.size
+    rng = np.random.default_rng([seed, 77])
+    n = int(counts.sum())
+    vt = math.sqrt(T_eV * W.E_CHARGE / W.M_E)
+    cell = np.repeat(np.arange(M, dtype=np.int32), counts)
+    vx, vy, vz = (rng.standard_normal(n) * vt for _ in range(3))
+    if shuffled:
+        p = rng.permutation(n)
+        vx, vy, vz, cell = vx[p], vy[p], vz[p], cell[p]
+    dt = 0.1 / W.nrl_nu_e(dens, T_eV, 10.0)
+    return W._base(M, vx=vx, vy=vy, vz=vz, cell=cell.astype(np.int32), inv_vol=np.full(M, dens / 1000.0),
+                   dt_cell=np.full(M, dt), lnlam_cell=np.full(M, 10.0), seed=seed, capacity=2 * n, steps=3,
+                   coulomb=True, neutral=True, precision="f64", dt=dt)
+
+
+CLASS_EDGES = [1, 2, 3, 5, 100, 2047, 2048, 2049, 4095, 4096, 4097, 9999, 12288, 12289, 30001, 32768, 32769,
+               49152]
+
+
+def _vel_err(v_gpu, v_ref):
+    """Per-particle |dv| / max(|v_ref|, 1e-3 v_rms)."""
+    d = np.sqrt(sum((a - b) ** 2 for a, b in zip(v_gpu, v_ref)))
+    nrm = np.sqrt(sum(b * b for b in v_ref))
+    floor = 1e-3 * np.sqrt(np.mean(nrm * nrm)) if nrm.size else 1.0
+    return d / np.maximum(nrm, floor)
+
+
+# ----------------------------------------------------------------------------- grouping, pairing
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_grouping_and_pair_order_bit_exact(L, orc, prec):
+    counts = CLASS_EDGES + ([65536] if prec == "f32" else [])
+    wl = big_cells_workload(counts, seed=4)
+    col = L.Collider.from_workload(wl, precision=L.F32 if prec == "f32" else L.F64)
+    col.load_workload(wl)
+    cs, perm, cnt = col.grouping()
+    ocounts, ocs, operm = orc.group(wl["cell"], wl["M"])
+    assert np.array_equal(cnt, ocounts)
+    assert np.array_equal(cs.astype(np.uint64), ocs)
+    for j in range(wl["M"]):
+        a, b = int(ocs[j]), int(ocs[j + 1])
+        assert np.array_equal(np.sort(perm[a:b]), operm[a:b]), j
+    for step in (0, 1, 12345):
+        gcs, gorder = col.pair_order(step)
+        ocs2, oorder = orc.pair_order(wl["cell"], wl["M"], wl["seed"], step)
+        assert np.array_equal(gcs.astype(np.uint64), ocs2)
+        bad = np.nonzero(gorder != oorder)[0]
+        assert bad.size == 0, f"step {step}: {bad.size} positions differ, first {bad[:5]}"
+    col.sync()
+
+
+def test_pair_order_ragged_shuffled(L, orc):
+    wl = W.ragged(M=41, mean_ppc=400, seed=9, shuffled=True)
+    col = L.Collider.from_workload(wl, precision=L.F64)
+    col.load_workload(wl)
+    gcs, gorder = col.pair_order(7)
+    ocs, oorder = orc.pair_order(wl["cell"], wl["M"], wl["seed"], 7)
+    assert np.array_equal(gorder, oorder)
+
+
+# ----------------------------------------------------------------------------- FP64 parity
+def _fp64_coulomb_case(L, orc, wl, steps=(0,)):
+    col = L.Collider.from_workload(wl, precision=L.F64, correction=0)
+    col.load_workload(wl)
+    st = orc.State(wl)
+    P = orc.make_params(wl)
+    worst = 0.0
+    for s in steps:
+        # single-step parity from an identical state
+        vx, vy, vz, cell, _ = col.read()
+        st.vx[:st.n], st.vy[:st.n], st.vz[:st.n] = vx, vy, vz
+        col.collide_coulomb(col.dt, s)
+        orc.coulomb(st, P, s)
+        gx, gy, gz, gc, _ = col.read()
+        col.sync()
+        err = _vel_err((gx, gy, gz), (st.vx[:st.n], st.vy[:st.n], st.vz[:st.n]))
+        worst = max(worst, float(err.max()))
+        assert err.max() <= FP64_TOL, (s, err.max(), int(err.argmax()))
+    return worst
+
+
+def test_fp64_coulomb_cfg1_reduced(L, orc):
+    wl = W.cfg1(M=16, ppc=1000)
+    _fp64_coulomb_case(L, orc, wl, steps=(0, 1, 2))
+
+
+def test_fp64_coulomb_all_classes(L, orc):
+    wl = big_cells_workload(CLASS_EDGES, seed=5)
+    _fp64_coulomb_case(L, orc, wl, steps=(3,))
+
+
+def test_fp64_neutral_step_and_append(L, orc):
+    wl = W.ragged(M=29, mean_ppc=300, seed=11, shuffled=True, T_eV=15.0)
+    wl["dt_cell"] = np.full(wl["M"], 4e-11)       # many e-n collisions, some ionizations
+    wl["x"] = np.arange(wl["vx"].size, dtype=np.float64) * 1e-3
+    col = L.Collider.from_workload(wl, precision=L.F64, correction=0)
+    col.load_workload(wl)
+    st = orc.State(wl)
+    P = orc.make_params(wl)
+    col.collide_neutral(col.dt, 5)
+    info = orc.neutral(st, P, 5)
+    gx, gy, gz, gc, gpos = col.read()
+    col.sync()
+    assert info["ionization"] > 0 and info["elastic"] > 0
+    assert gx.size == st.n, (gx.size, st.n)
+    assert np.array_equal(gc, st.cell[:st.n])
+    assert np.array_equal(gpos, st.x[:st.n])
+    err = _vel_err((gx, gy, gz), (st.vx[:st.n], st.vy[:st.n], st.vz[:st.n]))
+    assert err.max() <= FP64_TOL, (err.max(), int(err.argmax()))
+
+
+def test_fp64_fused_step_moments(L, orc):
+    wl = W.ragged(M=33, mean_ppc=350, seed=13, shuffled=False, T_eV=12.0)
+    wl["dt_cell"] = np.full(wl["M"], 1e-11)
+    col = L.Collider.from_workload(wl, precision=L.F64, correction=0)
+    col.load_workload(wl)
+    st = orc.State(wl)
+    P = orc.make_params(wl)
+    for s in range(3):
+        vx, vy, vz, cell, _ = col.read()
+        st.n = vx.size
+        st.vx[:st.n], st.vy[:st.n], st.vz[:st.n], st.cell[:st.n] = vx, vy, vz, cell
+        col.step(col.dt, s)
+        omom, ohist, _ = orc.step(st, P, s)
+        mom, hist = col.moments()
+        col.sync()
+        assert np.array_equal(mom[:, 0], omom[:, 0])
+        scale = np.maximum(np.abs(omom), 1e-300)
+        vscale = np.sqrt(omom[:, 5:8].sum(1, keepdims=True) / np.maximum(omom[:, :1], 1))
+        d = np.abs(mom - omom)
+        d[:, 2:5] /= np.maximum(vscale * np.maximum(omom[:, :1], 1), 1e-300)
+        d[:, [1, 5, 6, 7, 8, 9]] /= scale[:, [1, 5, 6, 7, 8, 9]]
+        d[:, 0] = 0
+        assert d.max() <= 1e-12, (s, d.max(), np.unravel_index(d.argmax(), d.shape))
+        assert np.array_equal(hist, ohist)
+        gx, gy, gz, _, _ = col.read()
+        err = _vel_err((gx, gy, gz), (st.vx[:st.n], st.vy[:st.n], st.vz[:st.n]))
+        assert err.max() <= FP64_TOL
+
+
+# ----------------------------------------------------------------------------- FP32 parity
+def _moment_errors(mom, omom, vth):
+    """Per-cell errors: N exact, sums of v over N v_th, sums of v^2 and speed sums relative."""
+    N = np.maximum(omom[:, 0], 1)
+    e = np.zeros_like(omom)
+    e[:, 0] = np.abs(mom[:, 0] - omom[:, 0])
+    e[:, 2:5] = np.abs(mom[:, 2:5] - omom[:, 2:5]) / (N[:, None] * vth)
+    for k in (5, 6, 7, 8, 9):
+        e[:, k] = np.abs(mom[:, k] - omom[:, k]) / np.maximum(np.abs(omom[:, k]), 1e-300)
+    e[omom[:, 9] == 0, 9] = np.abs(mom[omom[:, 9] == 0, 9]) > 0
+    return e
+
+
+def test_fp32_coulomb_moments(L, orc):
+    wl = W.cfg2(M=48, ppc=2000, steps=3)
+    wl["neutral"] = False
+    v32 = [wl[k].astype(np.float32) for k in ("vx", "vy", "vz")]
+    for k, v in zip(("vx", "vy", "vz"), v32):
+        wl[k] = v.astype(np.float64)       # the oracle starts from the same binary32 values
+    col = L.Collider.from_workload(wl, precision=L.F32)
+    col.load_workload(wl)
+    st = orc.State(wl)
+    P = orc.make_params(wl, correction=True)
+    vth = math.sqrt(2.0 * W.E_CHARGE / W.M_E)
+    for s in range(3):
+        col.collide_coulomb(wl["dt"], s)
+        orc.coulomb(st, P, s)
+        omom, _ = orc.moments(st, P)
+        mom, _ = col.moments()
+        col.sync()
+        e = _moment_errors(mom, omom, vth)
+        assert e[:, 0].max() == 0
+        assert e[:, 2:9].max() <= FP32_TOL, (s, e[:, 2:9].max(axis=0))
+
+
+def test_fp32_full_step_with_flip_accounting(L, orc):
+    wl = W.cfg2(M=32, ppc=2000, steps=1)
+    for k in ("vx", "vy", "vz"):
+        wl[k] = wl[k].astype(np.float32).astype(np.float64)
+    col = L.Collider.from_workload(wl, precision=L.F32)
+    col.load_workload(wl)
+    st = orc.State(wl)
+    P = orc.make_params(wl, correction=True)
+    vth = math.sqrt(2.0 * W.E_CHARGE / W.M_E)
+    orc.coulomb(st, P, 0)
+    probe = orc.State(wl)
+    probe.vx[:], probe.vy[:], probe.vz[:] = st.vx, st.vy, st.vz
+    dec = orc.neutral(probe, P, 0, with_decisions=True)
+    near = np.zeros(wl["M"], bool)
+    near[st.cell[:st.n][dec["margin"] < 1e-6]] = True
+    orc.neutral(st, P, 0)
+    omom, _ = orc.moments(st, P)
+    col.step(wl["dt"], 0)
+    mom, _ = col.moments()
+    col.sync()
+    e = _moment_errors(mom, omom, vth)
+    ok = ~near
+    assert near.sum() <= 2, near.sum()
+    assert e[ok, 0].max() == 0
+    assert e[ok][:, 2:9].max() <= FP32_TOL, e[ok][:, 2:9].max(axis=0)
+
+
+# ----------------------------------------------------------------------------- determinism, errors
+def test_determinism_graph_and_repeat(L):
+    wl = W.cfg2(M=16, ppc=3000, steps=1)
+    outs = []
+    for use_graph in (True, True, False):
+        col = L.Collider.from_workload(wl, precision=L.F32, use_graph=use_graph)
+        col.load_workload(wl)
+        col.run(wl["dt"], 0, 4)
+        outs.append(col.read())
+        col.sync()
+    for o in outs[1:]:
+        for a, b in zip(outs[0][:4], o[:4]):
+            assert np.array_equal(a, b)
+
+
+def test_capacity_overflow_reported(L):
+    wl = W.ragged(M=4, mean_ppc=500, seed=2, T_eV=60.0, with_empty=False)
+    wl["dt_cell"] = np.full(4, 2e-10)
+    col = L.Collider.from_workload(wl, precision=L.F64, capacity=wl["vx"].size)
+    col.load_workload(wl)
+    col.collide_neutral(col.dt, 0)
+    assert col.sync_code() == L.ECAPACITY
+
+
+def test_bad_cell_and_nonfinite_rejected(L):
+    wl = W.ragged(M=5, mean_ppc=20, seed=1, with_empty=False)
+    col = L.Collider.from_workload(wl, precision=L.F64)
+    bad = wl["cell"].copy()
+    bad[3] = 5
+    with pytest.raises(L.LtpcError) as ei:
+        col.load(wl["vx"], wl["vy"], wl["vz"], bad)
+    assert ei.value.code == L.EINVAL
+    vx = wl["vx"].copy()
+    vx[7] = np.nan
+    with pytest.raises(L.LtpcError) as ei:
+        col.load(vx, wl["vy"], wl["vz"], wl["cell"])
+    assert ei.value.code == L.ENONFINITE
