@@ -1,0 +1,442 @@
+"""Benchmark of the collision step on GB300: particle-updates/s and HBM roofline.
+
+Default workload (N=1): 4096 cells x 10000 electrons, FP32 velocities,
+Takizuka-Abe Coulomb + null-collision electron-neutral step + moments, fused
+per cell, replayed as a CUDA graph.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload cfg2|cfg1|cfg3|cfg4]
+
+With N > 1 (torchrun), every rank runs an independent replica of the workload
+(its own seed): the method shards by cell and instance with no exchange, so
+there is no data-path collective (weak scaling).  `--impl reference` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "collision particle-updates/s (FP32 batched vs FP64 plain) and % of HBM roofline"
+UNIT = "particle-updates/s"
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2508_06771_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """Per-launch DRAM bytes of the cell kernel from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    f = os.path.join(ROOT, "profiles", f"cells_{workload}_ncu.md")
+    if not os.path.exists(f):
+        return None
+    vals = {}
+    for line in open(f):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while a region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0, period_ms=50):
+        self.gpu, self.period = gpu_index, period_ms
+        self.proc = None
+
+    def __enter__(self):
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", f"-lms={self.period}"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.out.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.out.name):
+                f = [t.strip() for t in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        finally:
+            os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(name, seed, rank=0, cells=None):
+    from paper_2508_06771_gb300 import workloads as W
+    if name == "cfg2":
+        wl = W.cfg2(seed=seed, M=cells or 4096)
+        desc = f"cfg2: 1D grid of {wl['M']} cells x 10000 electrons (N0={wl['vx'].size:,}), FP32 SoA velocities, " \
+               "95% at 2 eV + 500/cell at 20 eV, Takizuka-Abe Coulomb + null-collision e-n (elastic, " \
+               "ionization >15.76 eV), fused per-cell moments"
+    elif name == "cfg1":
+        wl = W.cfg1(seed=seed)
+        desc = "cfg1: 64 cells x 1000 electrons, FP64, anisotropic Maxwellian, Coulomb only"
+    elif name == "cfg3":
+        wl = W.cfg3(seed=seed, dtype=np.float32)
+        desc = f"cfg3: 256x256 cells, log-uniform 16..65536 per cell (N0={wl['vx'].size:,}), FP32, NRL lnL, Coulomb"
+    elif name == "cfg4":
+        wl = W.cfg4(seed=seed, dtype=np.float32)
+        desc = f"cfg4: 64 instances, {wl['M']} cells, N0={wl['vx'].size:,}, FP32, per-instance dt, Coulomb"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return wl, desc
+
+
+def algorithmic_bytes_per_particle(prec):
+    """Cell kernel: read the id list (4 B), gather the velocities, write them back."""
+    es = 4 if prec == "f32" else 8
+    return 4 + 6 * es
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as orc
+    from paper_2508_06771_gb300 import workloads as W
+    orc.build()
+    # calibrate the oracle's cost per particle on one small cell block
+    wl_small = W.cfg2(M=64, ppc=10000, seed=0, blocks=[0]) if args.workload == "cfg2" else None
+    if args.workload != "cfg2":
+        wl_small = make_workload(args.workload, 0)[0]
+    full_wl_cells = 4096 if args.workload == "cfg2" else wl_small["M"]
+    st = orc.State(wl_small)
+    P = orc.make_params(wl_small, correction=True)
+    neutral = wl_small.get("neutral", False)
+    t0 = time.perf_counter()
+    orc.step(st, P, 0, True, neutral)
+    per_particle = (time.perf_counter() - t0) / max(1, st.n)
+    budget = 150.0
+    nsteps = args.steps + args.warmup
+    target = budget / nsteps / per_particle
+    ppc = wl_small["vx"].size / wl_small["M"]
+    cells = int(max(1, min(full_wl_cells, target // ppc)))
+    if args.workload == "cfg2":
+        blocks = list(range(max(1, (cells + W.BLOCK - 1) // W.BLOCK)))
+        wl = W.cfg2(seed=0, blocks=blocks)
+        wl = W.subset_cells(wl, np.arange(min(cells, len(blocks) * W.BLOCK)))
+    else:
+        wl = W.subset_cells(wl_small, np.arange(min(cells, wl_small["M"])))
+    st = orc.State(wl, capacity=2 * wl["vx"].size)
+    P = orc.make_params(wl, correction=True)
+    for s in range(args.warmup):
+        orc.step(st, P, s, True, neutral)
+    upd = 0
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        upd += st.n
+        orc.step(st, P, s, True, neutral)
+    el = time.perf_counter() - t0
+    v = upd / el
+    sample = f"{wl['M']} of the workload's cells ({st.n:,} particles), {args.steps} steps, FP64 oracle, 1 thread"
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": make_workload_desc(args.workload)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def make_workload_desc(name):
+    return {"cfg2": "cfg2: 4096 cells x 10000 electrons, FP32 Coulomb + e-n null collision",
+            "cfg1": "cfg1: 64 cells x 1000 electrons, FP64 Coulomb",
+            "cfg3": "cfg3: 256x256 log-uniform cells, FP32 Coulomb",
+            "cfg4": "cfg4: 64 instances, FP32 Coulomb"}[name]
+
+
+def cpu_baseline(workload, budget_s=12.0):
+    """The oracle as it stands on a bounded sample of the workload (rank 0, N=1)."""
+    import oracle as orc
+    from paper_2508_06771_gb300 import workloads as W
+    orc.build()
+    if workload == "cfg2":
+        wl = W.subset_cells(W.cfg2(seed=0, blocks=[0]), np.arange(16))
+        wl["capacity"] = 2 * wl["vx"].size
+        neutral = True
+    else:
+        full = make_workload(workload, 0)[0]
+        wl = W.subset_cells(full, np.arange(min(full["M"], 16)))
+        neutral = full.get("neutral", False)
+    st = orc.State(wl)
+    P = orc.make_params(wl, correction=True)
+    upd, s = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        upd += st.n
+        orc.step(st, P, s, True, neutral)
+        s += 1
+    el = time.perf_counter() - t0
+    return {"value": upd / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{wl['M']} cells ({wl['vx'].size:,} particles) of the workload, {s} full steps "
+                      f"(Coulomb{' + e-n' if neutral else ''} + moments), FP64, single thread, {el:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2508_06771_gb300 import build as B
+    from paper_2508_06771_gb300 import ltpc
+
+    torch.cuda.set_device(local_rank)
+    B.build()
+    wl, desc = make_workload(args.workload, seed=rank, cells=args.cells)
+    prec = "f32" if wl["precision"] == "f32" else "f64"
+    col = ltpc.Collider.from_workload(wl, precision=ltpc.F32 if prec == "f32" else ltpc.F64)
+    dt = col.dt
+    col.load_workload(wl)
+    n0 = col.count()
+    if args.autotune:
+        col.autotune(dt)
+    classes = col.classes()
+    stream = torch.cuda.current_stream()
+    step = 0
+    # warm-up (also captures the graph)
+    col.run(dt, step, args.warmup)
+    step += args.warmup
+    col.sync()
+    n_start = col.count()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- timed region: K graph replays, device-resident inputs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        col.run(dt, step, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    step += args.steps
+    ms = e0.elapsed_time(e1)
+    col.sync()
+    n_end = col.count()
+    updates = args.steps * (n_start + n_end) / 2.0      # particle count grows ~linearly through the run
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    u = torch.tensor([updates], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max, upd_all = float(t.item()), float(u.item())
+    value = upd_all / (ms_max / 1e3)
+    launches_per_step = 3 + len(classes)
+
+    # ---- per-kernel device times (CUDA events on the launching stream) for the roofline
+    nprof = min(max(args.steps, 5), 30)
+    per = []
+    for _ in range(nprof):
+        per.append(col.profile_step(dt, step))
+        step += 1
+    per = np.array(per)
+    avg = per.mean(0)
+    names = ["scatter"] + [f"cells_C{c['cluster']}x{c['threads']}" for c in classes] + ["regroup", "append"]
+    dom = int(np.argmax(avg))
+    n_now = col.count()
+    # cells of cfg-like workloads fall in one class; count the particles that class processes
+    counts = col.grouping()[2].astype(np.int64) if dom not in (0, len(names) - 2, len(names) - 1) else None
+    if counts is not None:
+        k = dom - 1
+        lo = classes[k - 1]["max_n"] if k > 0 else 0
+        hi = classes[k]["max_n"]
+        units = int(counts[(counts > lo) & (counts <= hi)].sum())
+        bpp = algorithmic_bytes_per_particle(prec)
+    else:
+        units, bpp = n_now, 8
+    alg_bytes = units * bpp
+    achieved = alg_bytes / (avg[dom] * 1e-3) / 1e9
+    peak, peak_src = peaks()
+    traffic = recorded_traffic(args.workload) if dom not in (0,) else None
+
+    # ---- FP64 plain form on the same workload (no graph), for the FP32-vs-FP64 comparison
+    fp64 = None
+    if prec == "f32" and not args.no_fp64:
+        colD = ltpc.Collider.from_workload(wl, precision=ltpc.F64, use_graph=False)
+        colD.load_workload(wl)
+        colD.run(dt, 0, 2)
+        colD.sync()
+        ns = max(3, min(10, args.steps // 10))
+        nA = colD.count()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        colD.run(dt, 2, ns)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        colD.sync()
+        nB = colD.count()
+        fms = f0.elapsed_time(f1)
+        fp64 = {"value": ns * (nA + nB) / 2.0 / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / ns,
+                "steps": ns, "form": "same kernels in binary64, one launch per class, no graph, no correction"}
+        fp64["fp32_speedup"] = value / world / fp64["value"]
+        colD.close()
+        del colD
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI: host buffers in, moments out, every step
+    e2e = None
+    if not args.no_e2e:
+        ne = max(2, min(10, args.steps // 20))
+        host = [torch.from_numpy(np.ascontiguousarray(wl[k], dtype=np.float32 if prec == "f32" else np.float64))
+                .pin_memory() for k in ("vx", "vy", "vz")]
+        hcell = torch.from_numpy(np.ascontiguousarray(wl["cell"], dtype=np.int32)).pin_memory()
+        mom = torch.empty((wl["M"], 10), dtype=torch.float64).pin_memory()
+        hist = torch.empty((wl["M"], 64), dtype=torch.int32).pin_memory()
+        hn = [h.numpy() for h in host]
+        col.load_host(hn[0], hn[1], hn[2], hcell.numpy())
+        col.step(dt, 0)
+        col.moments_host(mom.numpy(), hist.numpy())
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        upd_e = 0
+        for s in range(ne):
+            col.load_host(hn[0], hn[1], hn[2], hcell.numpy())
+            upd_e += n0
+            col.step(dt, s)
+            col.moments_host(mom.numpy(), hist.numpy())
+        torch.cuda.synchronize()
+        barrier()
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], dtype=torch.float64, device="cuda")
+        ue = torch.tensor([float(upd_e)], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            dist.all_reduce(ue, op=dist.ReduceOp.SUM)
+        es = 4 if prec == "f32" else 8
+        e2e = {"value": float(ue.item()) / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(n0 * (3 * es + 4)),
+               "d2h_bytes_per_step": int(wl["M"] * (10 * 8 + 64 * 4)), "steps": ne,
+               "path": "ltpc_load_particles(host, pinned) + ltpc_step + ltpc_moments(host)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded numpy generator, one replica per rank)",
+            "config": {"workload": desc, "cells": wl["M"], "particles_start": int(n0),
+                       "particles_end_of_timed": int(n_end), "precision": f"{prec} velocities and collision "
+                       "arithmetic, f64 per-cell sums", "graph": True,
+                       "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (
+                           n0 * (16 if prec == 'f32' else 28) / 1e6),
+                       "class_table": [f"C={c['cluster']} x {c['threads']} thr, cells<={c['max_n']}" for c in classes],
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": names[dom],
+                         "kernel_ms": float(avg[dom]), "algorithmic_bytes": int(alg_bytes),
+                         "bytes_per_particle": bpp, "peak_source": peak_src,
+                         "kernel_share": {n: float(a / avg.sum()) for n, a in zip(names, avg)}},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clocks,
+            "fp64_plain": fp64,
+            "ns_per_particle_step": ms_max * 1e6 / (upd_all / world),
+        }
+        print(json.dumps(line), flush=True)
+    col.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--cells", type=int, default=None, help="cfg2 only: number of cells (profiling cases)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

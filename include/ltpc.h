@@ -128,6 +128,14 @@ int ltpc_step(ltpc_ctx* ctx, double dt, int64_t step);
 /* nsteps consecutive ltpc_step calls for steps step0, step0+1, ... */
 int ltpc_run(ltpc_ctx* ctx, double dt, int64_t step0, int64_t nsteps);
 
+/* Tracing: one full step like ltpc_step but launched without a graph, with
+ * CUDA events recorded on the context's stream around every kernel of the
+ * pass.  ms[k] receives the device time of kernel k in launch order:
+ * 0 grouping scatter (CCS3), 1..C cell kernel of each cluster class (see
+ * ltpc_classes), C+1 regroup/offsets (CCS2), C+2 append of secondaries.
+ * *n_out = C + 3.  `capacity` is the length of ms.  Synchronizing. */
+int ltpc_profile_step(ltpc_ctx* ctx, double dt, int64_t step, float* ms, int32_t capacity, int32_t* n_out);
+
 /* Per-cell moments of the last pass: mom[10 j + k] (double) with k =
  * 0 N_j, 1 w N_j, 2-4 sum v_x, v_y, v_z, 5-7 sum v_x^2, v_y^2, v_z^2,
  * 8 sum sigma_el |v|, 9 sum sigma_ion(E) |v|; hist[64 j + b] (uint32):

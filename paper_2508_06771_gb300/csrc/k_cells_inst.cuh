@@ -24,11 +24,13 @@ struct CellKernel {
         cfg.numAttrs = 1;
         return cfg;
     }
+    // Raise the dynamic shared-memory limit once per process (not a stream
+    // operation, so it never runs inside a graph capture after the first call).
     static cudaError_t prepare()
     {
-        cudaError_t e = cudaFuncSetAttribute(k_cells<T, C, NT, ITEMS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
-        return e;
+        static cudaError_t once = cudaFuncSetAttribute(k_cells<T, C, NT, ITEMS>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        return once;
     }
     static cudaError_t occupancy(int* clusters)
     {

@@ -77,6 +77,7 @@ struct ltpc_ctx {
     ltpc_config cfg;
     Layout L;
     cudaStream_t stream;
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
     int device = 0, sms = 1;
     unsigned char* st = nullptr;   // d_state
     unsigned char* wk = nullptr;   // d_work
@@ -180,13 +181,17 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
 // Enqueue one pass: scatter (CCS3), the cell kernel per class, then the
 // bookkeeping that appends secondaries and regroups for the next pass.
 template <class T>
-int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out)
+int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out, cudaStream_t s,
+                 cudaEvent_t* ev = nullptr)
 {
     const Layout& L = ctx->L;
-    cudaStream_t s = ctx->stream;
     const int grid_stream = ctx->sms * 8;
+    int ei = 0;
+    auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[ei++], s) : cudaSuccess; };
+    CK(mark());
     CK(launch_scatter(ctx->s<int32_t>(L.cell), ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
                       grid_stream, s));
+    CK(mark());
     CellArgs<T> a = make_args<T>(ctx, flags);
     a.order_out = order_out;
     for (int k = 0; k < ctx->lists.n_classes; ++k) {
@@ -195,23 +200,28 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
         const CellKernelEntry& e = ctx->kernels[ctx->kernel_idx[k]];
         auto fn = reinterpret_cast<cudaError_t (*)(const CellArgs<T>&, cudaStream_t, int)>(e.launcher);
         CK(fn(a, s, ctx->grid[k]));
+        CK(mark());
     }
     CK(launch_regroup(ctx->cfg.n_cells, ctx->w<uint32_t>(L.counts), ctx->w<uint32_t>(L.cell_start),
                       ctx->w<uint32_t>(L.cs_prev), ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.ion_count),
                       ctx->w<uint32_t>(L.ion_off), ctx->lists, (unsigned long long)ctx->cfg.capacity, 1,
                       advance ? 1 : 0, ctx->ds, s));
+    CK(mark());
     CK(launch_append<T>(ctx->cfg.n_cells, ctx->w<uint32_t>(L.ion_off), ctx->w<uint32_t>(L.cs_prev),
                         ctx->w<uint32_t>(L.stage_l), ctx->w<T>(L.stage_vx), ctx->w<T>(L.stage_vy),
                         ctx->w<T>(L.stage_vz), ctx->s<T>(L.vx), ctx->s<T>(L.vy), ctx->s<T>(L.vz),
                         ctx->s<int32_t>(L.cell), ctx->cfg.has_position ? ctx->s<T>(L.x) : nullptr, ctx->ds,
                         ctx->sms * 2, s));
+    CK(mark());
     return LTPC_OK;
 }
 
-int enqueue(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out = nullptr)
+int enqueue(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out = nullptr, cudaStream_t s = nullptr,
+            cudaEvent_t* ev = nullptr)
 {
-    return ctx->cfg.precision == LTPC_F32 ? enqueue_pass<float>(ctx, flags, advance, order_out)
-                                          : enqueue_pass<double>(ctx, flags, advance, order_out);
+    if (!s) s = ctx->stream;
+    return ctx->cfg.precision == LTPC_F32 ? enqueue_pass<float>(ctx, flags, advance, order_out, s, ev)
+                                          : enqueue_pass<double>(ctx, flags, advance, order_out, s, ev);
 }
 
 int set_state(ltpc_ctx* ctx, int64_t step, double dt)
@@ -368,6 +378,7 @@ void ltpc_destroy(ltpc_ctx* ctx)
 {
     if (!ctx) return;
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
 
@@ -434,10 +445,13 @@ int ltpc_step(ltpc_ctx* ctx, double dt, int64_t step)
     }
     if (!ctx->gexec || ctx->graph_flags != flags) {
         if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        // Capture on the context's private stream (the caller's stream may be the
+        // legacy default stream, which cannot be captured); replay on the caller's.
         cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue(ctx, flags, true);
-        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue(ctx, flags, true, nullptr, ctx->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
         if (e != cudaSuccess) return fail_cuda(ctx, e);
         e = cudaGraphInstantiate(&ctx->gexec, g, 0);
@@ -449,6 +463,31 @@ int ltpc_step(ltpc_ctx* ctx, double dt, int64_t step)
     ctx->next_step = step + 1;
     ctx->cur_dt = dt;
     return LTPC_OK;
+}
+
+int ltpc_profile_step(ltpc_ctx* ctx, double dt, int64_t step, float* ms, int32_t capacity, int32_t* n_out)
+{
+    if (!ctx || !ms || !n_out) return LTPC_EINVAL;
+    const int nk = ctx->lists.n_classes + 3;   // scatter, classes..., regroup, append
+    if (capacity < nk) return LTPC_EINVAL;
+    cudaEvent_t ev[MAX_CLASSES + 4];
+    int made = 0, rc = LTPC_OK;
+    for (; made < nk + 1; ++made) {
+        cudaError_t e = cudaEventCreate(&ev[made]);
+        if (e != cudaSuccess) { rc = fail_cuda(ctx, e); break; }
+    }
+    if (rc == LTPC_OK) rc = set_state(ctx, step, dt);
+    if (rc == LTPC_OK) rc = enqueue(ctx, step_flags(ctx, true, true), true, nullptr, ctx->stream, ev);
+    if (rc == LTPC_OK) {
+        cudaError_t e = cudaEventSynchronize(ev[nk]);
+        for (int k = 0; k < nk && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+        if (e != cudaSuccess) rc = fail_cuda(ctx, e);
+        ctx->next_step = step + 1;
+        ctx->cur_dt = dt;
+    }
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    *n_out = nk;
+    return rc;
 }
 
 int ltpc_run(ltpc_ctx* ctx, double dt, int64_t step0, int64_t nsteps)

@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH):
             "ltpc_collide_neutral": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_step": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_run": (C.c_int, [vp, C.c_double, i64, i64]),
+            "ltpc_profile_step": (C.c_int, [vp, C.c_double, i64, C.POINTER(C.c_float), i32, C.POINTER(i32)]),
             "ltpc_moments": (C.c_int, [vp, vp, vp, C.c_int]),
             "ltpc_read_particles": (C.c_int, [vp, vp, vp, vp, vp, vp, C.POINTER(i64), C.c_int]),
             "ltpc_sync": (C.c_int, [vp]),
@@ -222,6 +223,13 @@ class Collider:
 
     def run(self, dt, step0, nsteps):
         self._check(self.L.ltpc_run(self.ctx, float(dt), int(step0), int(nsteps)), "run")
+
+    def profile_step(self, dt, step):
+        """Device milliseconds of each kernel of one (non-graph) step, in launch order."""
+        ms = (C.c_float * 16)()
+        n = C.c_int32()
+        self._check(self.L.ltpc_profile_step(self.ctx, float(dt), int(step), ms, 16, C.byref(n)), "profile_step")
+        return [ms[k] for k in range(n.value)]
 
     def sync(self):
         self._check(self.L.ltpc_sync(self.ctx), "sync")
