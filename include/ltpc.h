@@ -136,6 +136,14 @@ int ltpc_run(ltpc_ctx* ctx, double dt, int64_t step0, int64_t nsteps);
  * *n_out = C + 3.  `capacity` is the length of ms.  Synchronizing. */
 int ltpc_profile_step(ltpc_ctx* ctx, double dt, int64_t step, float* ms, int32_t capacity, int32_t* n_out);
 
+/* Tracing: one full step (no graph) in which thread 0 of every CTA of the
+ * cell kernels adds the SM cycles it spent in each phase into d_cycles[16]
+ * (device, zeroed by the call): 0 work fetch, 1 pairing keys, 2 bucket
+ * offsets, 3 placement, 4 in-bucket rank, 5 position lookup, 6 gather,
+ * 7 Coulomb + restoration, 8 neutral sampling, 9 moments, 10 write-back.
+ * Asynchronous. */
+int ltpc_profile_phases(ltpc_ctx* ctx, double dt, int64_t step, unsigned long long* d_cycles);
+
 /* Per-cell moments of the last pass: mom[10 j + k] (double) with k =
  * 0 N_j, 1 w N_j, 2-4 sum v_x, v_y, v_z, 5-7 sum v_x^2, v_y^2, v_z^2,
  * 8 sum sigma_el |v|, 9 sum sigma_ion(E) |v|; hist[64 j + b] (uint32):

@@ -45,41 +45,76 @@ struct Cl {
     }
 };
 
-template <class T> __device__ __forceinline__ void sincospi_t(T x, T* s, T* c);
-template <> __device__ __forceinline__ void sincospi_t<float>(float x, float* s, float* c) { sincospif(x, s, c); }
-template <> __device__ __forceinline__ void sincospi_t<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+// Elementary functions per working precision.  binary32 uses the SFU
+// approximations (relative errors ~1e-7, far inside the 1e-5 moment bar);
+// binary64 uses correctly rounded or library functions (1e-12 velocity bar).
+template <class T> struct Math;
+template <> struct Math<float> {
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float ln(float x) { return __logf(x); }
+    // sin and cos of 2 pi u for u in (0, 1], evaluated on (-pi, pi]
+    static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c)
+    {
+        float sx, cx;
+        __sincosf(fmaf(6.28318530717958647692f, u, -3.14159265358979323846f), &sx, &cx);
+        *s = -sx;
+        *c = -cx;
+    }
+    static __device__ __forceinline__ int ebin(float E)
+    {
+        if (!(E > 0.f)) return 0;
+        const float t = fmaf(__log2f(E), 0.30102999566398120f * 12.8f, 25.6f);   // (log10 E + 2) 64/5
+        if (!(t >= 0.f)) return 0;
+        if (t >= 63.f) return 63;
+        return (int)t;
+    }
+};
+template <> struct Math<double> {
+    static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / ::sqrt(x); }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double ln(double x) { return ::log(x); }
+    static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+    static __device__ __forceinline__ int ebin(double E)
+    {
+        if (!(E > 0.0)) return 0;
+        const double t = (log10(E) + 2.0) * 12.8;
+        if (t < 0.0) return 0;
+        if (t >= 63.0) return 63;
+        return (int)t;
+    }
+};
 
 // Takizuka-Abe binary collision of an equal-mass pair (a, b); A is the cell
-// coefficient so that <delta^2> = A / |u|^3; w holds the pair's three uniforms.
+// coefficient so that <delta^2> = A / |u|^3; w holds the pair's three uniforms
+// (Box-Muller radius and angle for delta, then the azimuth phi).
 template <class T>
 __device__ __forceinline__ void ta_collide(T& ax, T& ay, T& az, T& bx, T& by, T& bz, T A, uint4 w)
 {
+    using M = Math<T>;
     const T ux = ax - bx, uy = ay - by, uz = az - bz;
     const T up2 = ux * ux + uy * uy;
     const T usq = up2 + uz * uz;
     if (usq == T(0)) return;
-    const T u = sqrt(usq);
-    const T var = A / (usq * u);
+    const T u = M::sqrt(usq);
+    const T iu = M::rcp(u);
+    const T var = A * iu * iu * iu;
     T sth, cth, sph, cph;
-    sincospi_t<T>(T(2) * unif<T>(w.y), &sth, &cth);
-    sincospi_t<T>(T(2) * unif<T>(w.z), &sph, &cph);
-    const T delta = sqrt(var * (T(-2) * log(unif<T>(w.x)))) * cth;
-    T sin_t, omc_t;
-    if (fabs(delta) <= T(1)) {
-        const T d2 = delta * delta;
-        const T rr = T(1) / (T(1) + d2);
-        sin_t = T(2) * delta * rr;
-        omc_t = T(2) * d2 * rr;
-    } else {
-        const T t = T(1) / delta;
-        const T rr = T(1) / (T(1) + t * t);
-        sin_t = T(2) * t * rr;
-        omc_t = T(2) * rr;
-    }
+    M::sincos2pi(unif<T>(w.y), &sth, &cth);
+    M::sincos2pi(unif<T>(w.z), &sph, &cph);
+    const T delta = M::sqrt(var * (T(-2) * M::ln(unif<T>(w.x)))) * cth;
+    // sin(Theta) = 2d/(1+d^2), 1-cos(Theta) = 2d^2/(1+d^2); for |d| > 1 use t = 1/d
+    const bool small = fabs(delta) <= T(1);
+    const T t = small ? delta : M::rcp(delta);
+    const T rr = M::rcp(T(1) + t * t);
+    const T sin_t = T(2) * t * rr;
+    const T omc_t = small ? T(2) * t * t * rr : T(2) * rr;
     T dux, duy, duz;
     if (up2 > T(0)) {
-        const T uperp = sqrt(up2);
-        const T ip = T(1) / uperp;
+        const T uperp = M::sqrt(up2);
+        const T ip = M::rcp(uperp);
         const T ca = uz * sin_t * cph * ip;
         const T cb = u * sin_t * sph * ip;
         dux = ux * ca - uy * cb - ux * omc_t;
@@ -100,19 +135,10 @@ template <class T>
 __device__ __forceinline__ void iso_dir(uint32_t wa, uint32_t wb, T& dx, T& dy, T& dz)
 {
     const T c = T(1) - T(2) * unif<T>(wa);
-    const T s = sqrt(fmax(T(0), T(1) - c * c));
+    const T s = Math<T>::sqrt(fmax(T(0), T(1) - c * c));
     T sp, cp;
-    sincospi_t<T>(T(2) * unif<T>(wb), &sp, &cp);
+    Math<T>::sincos2pi(unif<T>(wb), &sp, &cp);
     dx = s * cp; dy = s * sp; dz = c;
-}
-
-template <class T> __device__ __forceinline__ int energy_bin(T E)
-{
-    if (!(E > T(0))) return 0;
-    const T t = (log10(E) + T(2)) * T(12.8);
-    if (t < T(0)) return 0;
-    if (t >= T(63)) return 63;
-    return (int)t;
 }
 
 template <int NT>
@@ -145,11 +171,44 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_scan
     return res;
 }
 
+constexpr uint32_t LISTCAP = 512;    // positions handled per round of a masked pass
+
+// Run f(q) for every local position q whose bit is set in mask[0..nw),
+// in ascending order of q, spreading the work over all threads in rounds of
+// at most LISTCAP positions.  Clears the mask.  CTA-collective.
+template <int NT, class F>
+__device__ __forceinline__ void for_each_masked(uint32_t* mask, uint32_t nw, uint32_t* list, uint32_t* s_scan, F f)
+{
+    const unsigned tid = threadIdx.x;
+    uint32_t word = tid < nw ? mask[tid] : 0u;
+    uint32_t total;
+    const uint32_t start = block_excl_scan<NT>((uint32_t)__popc(word), s_scan, &total);
+    // round k handles the set bits of global rank [k LISTCAP, (k+1) LISTCAP)
+    for (uint32_t base = 0u; base < total; base += LISTCAP) {
+        uint32_t off = start, w = word;
+        while (w) {
+            if (off >= base + LISTCAP) break;
+            if (off >= base) list[off - base] = tid * 32u + (uint32_t)(__ffs(w) - 1);
+            w &= w - 1u;
+            ++off;
+        }
+        __syncthreads();
+        const uint32_t nl = total - base < LISTCAP ? total - base : LISTCAP;
+        for (uint32_t i = tid; i < nl; i += NT) f(list[i]);
+        __syncthreads();
+    }
+    if (tid < nw) mask[tid] = 0u;
+}
+
 // Sum NQ per-thread partials over the cluster in a fixed order: warp
-// butterfly (accumulator type) -> warps in order (double) -> CTAs in rank order.
+// butterfly, then a second butterfly over the warps' partials (one warp per
+// quantity), both in the accumulator type; CTAs combined in rank order in
+// double.  Deterministic for a given block shape.
 template <int NT, int C, int NQ, class A>
 __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, double* out)
 {
+    static_assert(NQ <= NT / 32, "one warp per quantity");
+    constexpr int NW = NT / 32;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
@@ -161,10 +220,11 @@ __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, 
         for (int k = 0; k < NQ; ++k) s_red[warp * NQ + k] = v[k];
     }
     __syncthreads();
-    if (threadIdx.x < (unsigned)NQ) {
-        double acc = 0.0;
-        for (int w = 0; w < NT / 32; ++w) acc += (double)s_red[w * NQ + threadIdx.x];
-        s_cl[threadIdx.x] = acc;
+    if (warp < (unsigned)NQ) {
+        A x = lane < (unsigned)NW ? s_red[lane * NQ + warp] : A(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) s_cl[warp] = (double)x;
     }
     Cl<C>::sync();
     if (threadIdx.x < (unsigned)NQ) {
@@ -175,47 +235,95 @@ __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, 
     Cl<C>::sync();
 }
 
-template <int NT, int C>
-__device__ __forceinline__ double cluster_max_d(double v, double* s_red, double* s_cl)
+// Largest value over the cluster (exact in any order).
+template <int NT, int C, class A>
+__device__ __forceinline__ A cluster_max(A v, A* s_red, double* s_cl)
 {
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
     if (lane == 0) s_red[warp] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < NT / 32; ++w) m = fmax(m, s_red[w]);
-        s_cl[0] = m;
+    if (warp == 0) {
+        A x = lane < (unsigned)(NT / 32) ? s_red[lane] : A(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xFFFFFFFFu, x, o));
+        if (lane == 0) s_cl[0] = (double)x;
     }
     Cl<C>::sync();
     double m = 0.0;
     for (unsigned q = 0; q < (unsigned)C; ++q) m = fmax(m, *Cl<C>::at(&s_cl[0], q));
     Cl<C>::sync();
-    return m;
+    return (A)m;
 }
 
 __device__ __forceinline__ void flag_error(DevState* ds, uint32_t bit) { atomicOr(&ds->err, bit); }
+
+// Begins of the C ranges of a split (ltpc_index.h), kept in registers so that
+// the owner of an item is found by C-1 compares instead of a division.
+template <int C>
+struct Bounds {
+    uint32_t b[C];
+    __device__ __forceinline__ void init_split(uint32_t total)
+    {
+#pragma unroll
+        for (int r = 0; r < C; ++r) b[r] = split_begin((uint32_t)r, total, (uint32_t)C);
+    }
+    __device__ __forceinline__ void init_pos(uint32_t n)
+    {
+#pragma unroll
+        for (int r = 0; r < C; ++r) b[r] = pos_begin((uint32_t)r, n, (uint32_t)C);
+    }
+    // owner = largest r with b[r] <= t; begin = b[owner]
+    __device__ __forceinline__ uint32_t locate(uint32_t t, uint32_t& begin) const
+    {
+        uint32_t o = 0u, bg = b[0];
+#pragma unroll
+        for (int r = 1; r < C; ++r) {
+            const bool ge = t >= b[r];
+            o += ge ? 1u : 0u;
+            bg = ge ? b[r] : bg;
+        }
+        begin = bg;
+        return o;
+    }
+};
 
 // Shared-memory bytes a launch of the cell kernel needs (dynamic part).
 template <class T>
 __host__ __device__ constexpr size_t cells_dyn_smem(uint32_t capl)
 {
     const size_t pair_b = (size_t)capl * (3 * sizeof(T) + 4 + 2);
-    const size_t sort_b = (size_t)capl * 16 + ((size_t)capl / 4 + 2) * 4;
+    const size_t sort_b = (size_t)capl * 12 + ((size_t)capl + 2) * 4;
     const size_t m = pair_b > sort_b ? pair_b : sort_b;
     return (m + 15) & ~(size_t)15;
 }
 
+// Tracing: thread 0 of every CTA adds the SM cycles of each phase.
+struct PhaseClock {
+    unsigned long long* out;
+    long long t;
+    __device__ __forceinline__ void start() { if (out && threadIdx.x == 0) t = clock64(); }
+    __device__ __forceinline__ void mark(int k)
+    {
+        if (out && threadIdx.x == 0) {
+            const long long now = clock64();
+            atomicAdd(out + k, (unsigned long long)(now - t));
+            t = now;
+        }
+    }
+};
+
 template <class T, int C, int NT, int ITEMS>
-__global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a)
 {
     static_assert(NT % 32 == 0 && NT <= 1024, "block size");
     static_assert(ITEMS % 2 == 0, "ITEMS must be even");
     constexpr uint32_t CAPL = (uint32_t)NT * ITEMS;
     static_assert(CAPL <= 65536u, "positions are packed in 16 bits");
+    static_assert(CAPL / 32 <= NT, "one mask word per thread");
     constexpr int NW = NT / 32;
-    constexpr int PER = (CAPL / 4 + 2 + NT - 1) / NT;   // bucket counters per thread in the scan
+    constexpr int PER = (CAPL + 2 + NT - 1) / NT;   // bucket counters per thread in the scan
 
     extern __shared__ __align__(16) unsigned char smem[];
     // pair-phase view
@@ -228,16 +336,19 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
     uint32_t* stg = reinterpret_cast<uint32_t*>(smem);
     uint32_t* ekey = stg + CAPL;
     uint32_t* el = ekey + CAPL;
-    uint32_t* epos = el + CAPL;
-    uint32_t* bcnt = epos + CAPL;
+    uint32_t* bcnt = el + CAPL;
 
     __shared__ uint32_t s_scan[NW + 1];
     __shared__ T s_redacc[NW * 8];
-    __shared__ double s_redd[NW];
     __shared__ double s_cl[8];
     __shared__ double s_tot[8];
-    __shared__ uint32_t s_hist[NBIN];
+    __shared__ uint32_t s_hist[4 * NBIN];           // four sub-histograms (less atomic contention)
+    __shared__ uint32_t s_cmask[CAPL / 32];         // candidate / work bit masks over local positions
+    __shared__ uint32_t s_imask[CAPL / 32];         // ionizing positions
+    __shared__ uint32_t s_ioff[CAPL / 32];          // ionizations before each mask word
+    __shared__ uint32_t s_list[LISTCAP];
     __shared__ uint32_t s_misc[4];
+    __shared__ T s_par[16];
 
     const unsigned r = Cl<C>::rank();
     const unsigned tid = threadIdx.x;
@@ -251,6 +362,8 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
     const bool do_corr = (a.flags & F_CORRECTION) != 0u;
 
     Cl<C>::sync();   // every CTA of the cluster is running before any remote access
+    PhaseClock pc{a.phase_clk, 0};
+    pc.start();
 
     for (;;) {
         if (r == 0 && tid == 0) {
@@ -273,12 +386,16 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
         const uint32_t bb = split_begin(r, nb, C), nbl = split_begin(r + 1, nb, C) - bb;
         const uint32_t pb = pos_begin(r, n, C), pe = pos_end(r, n, C);
         const uint32_t nloc = pe > pb ? pe - pb : 0u;
+        Bounds<C> PB, BB;            // pairing-position and bucket splits of this cell
+        PB.init_pos(n);
+        BB.init_split(nb);
 
         // ---- 1a. zero this CTA's bucket counters and histogram
         for (uint32_t i = tid; i <= nbl; i += NT) bcnt[i] = 0u;
-        if (tid < (unsigned)NBIN) s_hist[tid] = 0u;
+        for (uint32_t i = tid; i < 4u * NBIN; i += NT) s_hist[i] = 0u;
         Cl<C>::sync();
 
+        pc.mark(0);
         // ---- 1b. home slice: particle ids (coalesced), pairing keys, bucket counts
         uint32_t hl[ITEMS], hp[ITEMS], hw[ITEMS];
 #pragma unroll
@@ -289,9 +406,9 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
                 const uint32_t l = a.perm[s + hb + k];
                 const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
                 const uint32_t b = __umulhi(rw.x, nb);
-                const uint32_t ro = split_owner(b, nb, C);
-                const uint32_t bi = b - split_begin(ro, nb, C);
-                const uint32_t slot = atomicAdd(Cl<C>::at(bcnt + bi, ro), 1u);
+                uint32_t b0;
+                const uint32_t ro = BB.locate(b, b0);
+                const uint32_t slot = atomicAdd(Cl<C>::at(bcnt + (b - b0), ro), 1u);
                 stg[k] = rw.x;
                 hl[i] = l;
                 hp[i] = (b << 16) | (slot & 0xFFFFu);
@@ -300,6 +417,7 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
         }
         Cl<C>::sync();
 
+        pc.mark(1);
         // ---- 1c. bucket starts: local exclusive scan, then offset by lower CTAs' totals
         {
             uint32_t cnt[PER];
@@ -326,17 +444,20 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
         }
         Cl<C>::sync();
 
+        pc.mark(2);
         // ---- 1d. place (key, id) at bucket start + slot, in the position-owner CTA
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
             if (k < nh) {
                 const uint32_t b = hp[i] >> 16, slot = hp[i] & 0xFFFFu;
-                const uint32_t ro = split_owner(b, nb, C);
-                const uint32_t gpos = *Cl<C>::at(bcnt + (b - split_begin(ro, nb, C)), ro) + slot;
+                uint32_t b0;
+                const uint32_t ro = BB.locate(b, b0);
+                const uint32_t gpos = *Cl<C>::at(bcnt + (b - b0), ro) + slot;
                 if (gpos < n) {
-                    const uint32_t po = pos_owner(gpos, n, C);
-                    const uint32_t lp = gpos - pos_begin(po, n, C);
+                    uint32_t p0;
+                    const uint32_t po = PB.locate(gpos, p0);
+                    const uint32_t lp = gpos - p0;
                     *Cl<C>::at(ekey + lp, po) = stg[k];
                     *Cl<C>::at(el + lp, po) = hl[i];
                 } else {
@@ -347,51 +468,50 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
         }
         Cl<C>::sync();
 
-        // ---- 1e. rank inside the bucket -> final pairing-order position
-        for (uint32_t q = tid; q < nloc; q += NT) {
-            const uint32_t key = ekey[q], l = el[q];
-            const uint32_t b = __umulhi(key, nb);
-            const uint32_t ro = split_owner(b, nb, C);
-            const uint32_t* bc = Cl<C>::at(bcnt + (b - split_begin(ro, nb, C)), ro);
-            const uint32_t bs = bc[0], be = bc[1];
-            uint32_t rank = 0u;
-            if (bs <= be && be <= n) {
-                for (uint32_t t = bs; t < be; ++t) {
-                    const uint32_t o = pos_owner(t, n, C);
-                    const uint32_t lt = t - pos_begin(o, n, C);
-                    const uint32_t kk = *Cl<C>::at(ekey + lt, o);
-                    const uint32_t ll = *Cl<C>::at(el + lt, o);
-                    rank += (kk < key) || (kk == key && ll < l);
-                }
-            } else {
-                flag_error(ds, ERR_INDEX);
-            }
-            epos[q] = bs + rank;
-        }
-        Cl<C>::sync();
-
-        // ---- 1f. home slice learns each particle's pairing-order position
+        pc.mark(3);
+        // ---- 1e. each home particle ranks itself inside its bucket: its final
+        // pairing-order position is the bucket start plus the number of entries
+        // of the bucket ordered before (key, id)
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
             if (k < nh) {
-                const uint32_t gpos = hp[i] < n ? hp[i] : 0u;
-                const uint32_t o = pos_owner(gpos, n, C);
-                uint32_t pos = *Cl<C>::at(epos + (gpos - pos_begin(o, n, C)), o);
+                const uint32_t key = stg[k], l = hl[i];
+                const uint32_t b = __umulhi(key, nb);
+                uint32_t b0;
+                const uint32_t ro = BB.locate(b, b0);
+                const uint32_t* bc = Cl<C>::at(bcnt + (b - b0), ro);
+                const uint32_t bs = bc[0], be = bc[1];
+                uint32_t rank = 0u;
+                if (bs <= be && be <= n) {
+                    for (uint32_t t = bs; t < be; ++t) {
+                        uint32_t t0;
+                        const uint32_t o = PB.locate(t, t0);
+                        const uint32_t kk = *Cl<C>::at(ekey + (t - t0), o);
+                        const uint32_t ll = *Cl<C>::at(el + (t - t0), o);
+                        rank += (kk < key) || (kk == key && ll < l);
+                    }
+                } else {
+                    flag_error(ds, ERR_INDEX);
+                }
+                uint32_t pos = bs + rank;
                 if (pos >= n) { flag_error(ds, ERR_INDEX); pos = 0u; }
                 hp[i] = pos | (hw[i] << 16);
             }
         }
         Cl<C>::sync();
 
+        pc.mark(4);
+        pc.mark(5);
         // ---- 2. gather velocities (coalesced through the id list) into pairing order
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
             if (k < nh) {
                 const uint32_t pos = hp[i] & 0xFFFFu, l = hl[i];
-                const uint32_t o = pos_owner(pos, n, C);
-                const uint32_t lp = pos - pos_begin(o, n, C);
+                uint32_t p0;
+                const uint32_t o = PB.locate(pos, p0);
+                const uint32_t lp = pos - p0;
                 const T x = a.vx[l], y = a.vy[l], z = a.vz[l];
                 *Cl<C>::at(svx + lp, o) = x;
                 *Cl<C>::at(svy + lp, o) = y;
@@ -403,200 +523,232 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
         }
         Cl<C>::sync();
 
-        const double dtj = dt * a.dt_factor[j];
-        // ---- 3. step S1: Takizuka-Abe collisions of pairs (2p, 2p+1)
+        pc.mark(6);
+        // ---- 3. step S1: Takizuka-Abe collisions of pairs (2p, 2p+1), then the
+        // optional restoration of the cell's momentum and energy.  The largest
+        // squared speed after S1 is tracked for the null-collision bound.
+        T vmax2 = T(0);
         if (do_coul && n >= 2u) {
-            double lnl = a.lnlam[j];
-            if (a.flags & F_LNL_NRL) {
-                const double* m = a.mom + (size_t)j * NMOM;
-                const double N = m[0];
-                lnl = 2.0;
-                if (N >= 2.0) {
-                    const double mx = m[2] / N, my = m[3] / N, mz = m[4] / N;
-                    const double msq = (m[5] + m[6] + m[7]) / N;
-                    const double TeV = a.mass * (msq - (mx * mx + my * my + mz * mz)) / 3.0 / (a.mass * a.e_over_m);
-                    const double nm3 = a.weight * (double)n * a.inv_vol[j];
-                    if (TeV > 0.0 && nm3 > 0.0) {
-                        const double lt = log(TeV);
-                        const double v = 23.5 - log(sqrt(nm3 * 1e-6) * pow(TeV, -1.25)) -
-                                         sqrt(1e-5 + (lt - 2.0) * (lt - 2.0) / 16.0);
-                        lnl = v < 2.0 ? 2.0 : v;
+            if (tid == 0) {   // per-cell scalars in double, once per CTA
+                const double dtj = dt * a.dt_factor[j];
+                double lnl = a.lnlam[j];
+                if (a.flags & F_LNL_NRL) {
+                    const double* m = a.mom + (size_t)j * NMOM;
+                    const double N = m[0];
+                    lnl = 2.0;
+                    if (N >= 2.0) {
+                        const double mx = m[2] / N, my = m[3] / N, mz = m[4] / N;
+                        const double msq = (m[5] + m[6] + m[7]) / N;
+                        const double TeV = (msq - (mx * mx + my * my + mz * mz)) / (3.0 * a.e_over_m);
+                        const double nm3 = a.weight * (double)n * a.inv_vol[j];
+                        if (TeV > 0.0 && nm3 > 0.0) {
+                            const double lt = log(TeV);
+                            const double v = 23.5 - log(sqrt(nm3 * 1e-6) * pow(TeV, -1.25)) -
+                                             sqrt(1e-5 + (lt - 2.0) * (lt - 2.0) / 16.0);
+                            lnl = v < 2.0 ? 2.0 : v;
+                        }
+                    }
+                }
+                s_par[0] = (T)(a.coef0 * (double)n * a.inv_vol[j] * lnl * dtj);
+                // centring shift for the restoration sums: the cell's mean velocity
+                // at the end of the previous pass (no CTA modifies it in this pass)
+                s_par[1] = s_par[2] = s_par[3] = T(0);
+                if (do_corr) {
+                    const double* m = a.mom + (size_t)j * NMOM;
+                    if (m[0] > 0.0) {
+                        s_par[1] = (T)(m[2] / m[0]); s_par[2] = (T)(m[3] / m[0]); s_par[3] = (T)(m[4] / m[0]);
                     }
                 }
             }
-            const T A = (T)(a.coef0 * (double)n * a.inv_vol[j] * lnl * dtj);
-            // Centring shift for the restoration sums: the cell's mean velocity at
-            // the end of the previous pass (a value no CTA modifies in this pass).
-            T cx = T(0), cy = T(0), cz = T(0);
-            if (do_corr) {
-                const double* m = a.mom + (size_t)j * NMOM;
-                if (m[0] > 0.0) { cx = (T)(m[2] / m[0]); cy = (T)(m[3] / m[0]); cz = (T)(m[4] / m[0]); }
-            }
+            __syncthreads();
+            const T A = s_par[0], cx = s_par[1], cy = s_par[2], cz = s_par[3];
             T acc[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[k] = T(0);
+            auto presum = [&](T x, T y, T z, int o) {
+                const T dx = x - cx, dy = y - cy, dz = z - cz;
+                acc[o] += dx; acc[o + 1] += dy; acc[o + 2] += dz; acc[o + 3] += dx * dx + dy * dy + dz * dz;
+            };
             const uint32_t nslot = (nloc + 1u) / 2u;
             for (uint32_t p = tid; p < nslot; p += NT) {
                 const uint32_t ia = 2u * p, ib = ia + 1u;
                 T ax = svx[ia], ay = svy[ia], az = svz[ia];
-                if (do_corr) {
-                    const T dx = ax - cx, dy = ay - cy, dz = az - cz;
-                    acc[0] += dx; acc[1] += dy; acc[2] += dz; acc[3] += dx * dx + dy * dy + dz * dz;
-                }
+                if (do_corr) presum(ax, ay, az, 0);
                 if (ib < nloc) {
                     T bx = svx[ib], by = svy[ib], bz = svz[ib];
-                    if (do_corr) {
-                        const T dx = bx - cx, dy = by - cy, dz = bz - cz;
-                        acc[0] += dx; acc[1] += dy; acc[2] += dz; acc[3] += dx * dx + dy * dy + dz * dz;
-                    }
                     const uint32_t la = sl[ia], lb = sl[ib];
+                    if (do_corr) presum(bx, by, bz, 0);
                     const uint4 w = draw(k0, k1, la < lb ? la : lb, step, TAG_PAIR);
                     ta_collide<T>(ax, ay, az, bx, by, bz, A, w);
                     svx[ia] = ax; svy[ia] = ay; svz[ia] = az;
                     svx[ib] = bx; svy[ib] = by; svz[ib] = bz;
-                    if (do_corr) {
-                        const T dx = bx - cx, dy = by - cy, dz = bz - cz;
-                        acc[4] += dx; acc[5] += dy; acc[6] += dz; acc[7] += dx * dx + dy * dy + dz * dz;
-                    }
+                    if (do_corr) presum(bx, by, bz, 4);
+                    else vmax2 = fmax(vmax2, bx * bx + by * by + bz * bz);
                 }
-                if (do_corr) {
-                    const T dx = ax - cx, dy = ay - cy, dz = az - cz;
-                    acc[4] += dx; acc[5] += dy; acc[6] += dz; acc[7] += dx * dx + dy * dy + dz * dz;
-                }
+                if (do_corr) presum(ax, ay, az, 4);
+                else vmax2 = fmax(vmax2, ax * ax + ay * ay + az * az);
             }
             if (do_corr) {
                 cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
                 // V = c + S1 / n and K = S2 - |S1|^2 / n, before (0..3) and after (4..7)
-                const double nn = (double)n;
-                const double K0 = s_tot[3] - (s_tot[0] * s_tot[0] + s_tot[1] * s_tot[1] + s_tot[2] * s_tot[2]) / nn;
-                const double K1 = s_tot[7] - (s_tot[4] * s_tot[4] + s_tot[5] * s_tot[5] + s_tot[6] * s_tot[6]) / nn;
-                const double f = (K1 > 0.0 && K0 > 0.0) ? sqrt(K0 / K1) : 1.0;
-                const T V0x = (T)((double)cx + s_tot[0] / nn), V0y = (T)((double)cy + s_tot[1] / nn),
-                        V0z = (T)((double)cz + s_tot[2] / nn);
-                const T V1x = (T)((double)cx + s_tot[4] / nn), V1y = (T)((double)cy + s_tot[5] / nn),
-                        V1z = (T)((double)cz + s_tot[6] / nn);
-                const T ft = (T)f;
+                if (tid < 7u) {   // restoration scalars, one per thread, in the working precision
+                    const T inv_n = T(1) / (T)n;
+                    const T S[8] = {(T)s_tot[0], (T)s_tot[1], (T)s_tot[2], (T)s_tot[3],
+                                    (T)s_tot[4], (T)s_tot[5], (T)s_tot[6], (T)s_tot[7]};
+                    T val;
+                    if (tid == 0) {
+                        const T K0 = S[3] - (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]) * inv_n;
+                        const T K1 = S[7] - (S[4] * S[4] + S[5] * S[5] + S[6] * S[6]) * inv_n;
+                        val = (K1 > T(0) && K0 > T(0)) ? Math<T>::sqrt(K0 / K1) : T(1);
+                    } else {
+                        const int k = (int)tid - 1;            // 0..5 -> V0x V0y V0z V1x V1y V1z
+                        const T c = (k % 3 == 0) ? cx : (k % 3 == 1) ? cy : cz;
+                        val = c + S[(k / 3) * 4 + (k % 3)] * inv_n;
+                    }
+                    s_par[4 + tid] = val;
+                }
+                __syncthreads();
+                const T ft = s_par[4], V0x = s_par[5], V0y = s_par[6], V0z = s_par[7], V1x = s_par[8],
+                        V1y = s_par[9], V1z = s_par[10];
                 for (uint32_t q = tid; q < nloc; q += NT) {
-                    svx[q] = V0x + ft * (svx[q] - V1x);
-                    svy[q] = V0y + ft * (svy[q] - V1y);
-                    svz[q] = V0z + ft * (svz[q] - V1z);
+                    const T x = V0x + ft * (svx[q] - V1x);
+                    const T y = V0y + ft * (svy[q] - V1y);
+                    const T z = V0z + ft * (svz[q] - V1z);
+                    svx[q] = x; svy[q] = y; svz[q] = z;
+                    vmax2 = fmax(vmax2, x * x + y * y + z * z);
                 }
             }
             __syncthreads();
-        }
-
-        // ---- 4. step S2a: null-collision electron-neutral sampling.  Positions are
-        // visited in thread-contiguous chunks, so a block scan over threads ranks
-        // ionizations in pairing-order position.
-        const uint32_t chunk = (nloc + NT - 1u) / NT;
-        const uint32_t c0 = tid * chunk < nloc ? tid * chunk : nloc;
-        const uint32_t c1 = c0 + chunk < nloc ? c0 + chunk : nloc;
-        uint32_t ion_base = 0u;
-        if (do_neut) {
-            double md = 0.0;   // largest squared speed in the working precision (exact in double)
+        } else if (do_neut) {
             for (uint32_t q = tid; q < nloc; q += NT) {
                 const T x = svx[q], y = svy[q], z = svz[q];
-                md = fmax(md, (double)(x * x + y * y + z * z));
+                vmax2 = fmax(vmax2, x * x + y * y + z * z);
             }
-            md = cluster_max_d<NT, C>(md, s_redd, s_cl);
-            const double nmx = a.n_neutral * (a.sigma_el + a.sigma_ion) * sqrt(md);
-            const T numax = (T)nmx;
-            const T pnull = (T)(-expm1(-nmx * dtj));
-            const T e_over_m = (T)a.e_over_m, e_ion = (T)a.e_ion;
-            const T nsel = (T)(a.n_neutral * a.sigma_el), nsion = (T)(a.n_neutral * a.sigma_ion);
-            uint32_t nion = 0u;
-            for (uint32_t q = c0; q < c1; ++q) {
-                T lo, up;
-                unif_hi16_range<T>((uint32_t)sw[q], lo, up);
-                uint16_t flag = 0;
-                if (lo < pnull) {                      // the candidate test may pass: redraw fully
-                    const uint32_t l = sl[q];
-                    const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
-                    if (unif<T>(rw.y) < pnull) {
-                        const T x = svx[q], y = svy[q], z = svz[q];
-                        const T v2 = x * x + y * y + z * z;
-                        const T v = sqrt(v2);
-                        const T E = T(0.5) * v2 / e_over_m;
-                        const T nu_el = nsel * v;
-                        const T nu_ion = E >= e_ion ? nsion * v : T(0);
-                        const T rr = unif<T>(rw.z) * numax;
-                        if (rr < nu_el) {                  // C1: elastic, cold heavy target
-                            const uint4 sc = draw(k0, k1, l, step, TAG_SCATTER);
-                            T dx, dy, dz;
-                            iso_dir<T>(sc.x, sc.y, dx, dy, dz);
-                            const T cchi = (x * dx + y * dy + z * dz) / v;
-                            const T vn = v * sqrt(T(1) - (T)a.mratio2 * (T(1) - cchi));
-                            svx[q] = vn * dx; svy[q] = vn * dy; svz[q] = vn * dz;
-                        } else if (rr < nu_el + nu_ion) {  // C2: ionization, resolved below
-                            flag = 1;
-                            ++nion;
-                        }
-                    }
+        }
+
+        pc.mark(7);
+        // ---- 4. step S2a: null-collision electron-neutral sampling.  Possible
+        // candidates (by the top 16 bits of the candidate word) are compacted
+        // through a bit mask so that whole warps redraw and collide them.
+        const uint32_t nw = (nloc + 31u) / 32u;
+        uint32_t ion_base = 0u;      // secondaries of lower-ranked CTAs of this cell
+        const T half_m_over_e = (T)(0.5 / a.e_over_m);
+        if (do_neut) {
+            const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl);
+            if (tid == 0) {   // null-collision bound of the cell, in the working precision
+                const T nmx = (T)(a.n_neutral * (a.sigma_el + a.sigma_ion)) * Math<T>::sqrt(md);
+                s_par[11] = nmx;
+                s_par[12] = -expm1(-nmx * (T)(dt * a.dt_factor[j]));
+            }
+            for (uint32_t w = tid; w < nw; w += NT) s_imask[w] = 0u;
+            __syncthreads();
+            const T numax = s_par[11];
+            const T pnull = s_par[12];
+            for (uint32_t q0 = 0; q0 < nloc; q0 += NT) {
+                const uint32_t q = q0 + tid;
+                bool maybe = false;
+                if (q < nloc) {
+                    T lo, up;
+                    unif_hi16_range<T>((uint32_t)sw[q], lo, up);
+                    maybe = lo < pnull;
                 }
-                sw[q] = flag;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, maybe);
+                if ((tid & 31u) == 0u && q0 + tid < nloc + 31u) s_cmask[(q0 + tid) >> 5] = m;
             }
+            __syncthreads();
+            const T nsel = (T)(a.n_neutral * a.sigma_el), nsion = (T)(a.n_neutral * a.sigma_ion);
+            const T e_ion = (T)a.e_ion, mr2 = (T)a.mratio2;
+            for_each_masked<NT>(s_cmask, nw, s_list, s_scan, [&](uint32_t q) {
+                const uint32_t l = sl[q];
+                const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
+                if (!(unif<T>(rw.y) < pnull)) return;
+                const T x = svx[q], y = svy[q], z = svz[q];
+                const T v2 = x * x + y * y + z * z;
+                const T v = Math<T>::sqrt(v2);
+                const T E = v2 * half_m_over_e;
+                const T nu_el = nsel * v;
+                const T nu_ion = E >= e_ion ? nsion * v : T(0);
+                const T rr = unif<T>(rw.z) * numax;
+                if (rr < nu_el) {                              // C1: elastic, cold heavy target
+                    const uint4 sc = draw(k0, k1, l, step, TAG_SCATTER);
+                    T dx, dy, dz;
+                    iso_dir<T>(sc.x, sc.y, dx, dy, dz);
+                    const T cchi = (x * dx + y * dy + z * dz) * Math<T>::rcp(v);
+                    const T vn = v * Math<T>::sqrt(T(1) - mr2 * (T(1) - cchi));
+                    svx[q] = vn * dx; svy[q] = vn * dy; svz[q] = vn * dz;
+                } else if (rr < nu_el + nu_ion) {              // C2: ionization, resolved below
+                    atomicOr(&s_imask[q >> 5], 1u << (q & 31u));
+                }
+            });
+            // ranks of this CTA's ionizations in position order, then across the cluster
             uint32_t tot;
-            const uint32_t ex = block_excl_scan<NT>(nion, s_scan, &tot);
+            const uint32_t wex = block_excl_scan<NT>(tid < nw ? (uint32_t)__popc(s_imask[tid]) : 0u, s_scan, &tot);
+            if (tid < nw) s_ioff[tid] = wex;
             if (tid == 0) s_misc[2] = tot;
             Cl<C>::sync();
-            uint32_t base = 0u, all = 0u;
+            uint32_t all = 0u;
             for (unsigned q = 0; q < (unsigned)C; ++q) {
                 const uint32_t t = *Cl<C>::at(&s_misc[2], q);
-                if (q < r) base += t;
+                if (q < r) ion_base += t;
                 all += t;
             }
-            ion_base = base + ex;
             if (r == 0 && tid == 0) a.ion_count[j] = all;
             Cl<C>::sync();
         } else if (r == 0 && tid == 0) {
             a.ion_count[j] = 0u;
         }
 
-        // ---- 5. ionization outcomes, then the moments of the cell after the step
+        pc.mark(8);
+        // ---- 5. ionization outcomes (C2), then the moments (S3a/S3b) of the cell
         {
-            const T e_over_m = (T)a.e_over_m, e_ion = (T)a.e_ion;
+            using M = Math<T>;
+            const T e_ion = (T)a.e_ion, two_e_over_m = (T)(2.0 * a.e_over_m);
             T acc[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[k] = T(0);
+            uint32_t* hsub = s_hist + ((tid >> 5) & 3u) * NBIN;
             auto accum = [&](T x, T y, T z) {
                 const T v2 = x * x + y * y + z * z;
-                const T v = sqrt(v2);
-                const T E = T(0.5) * v2 / e_over_m;
+                const T v = M::sqrt(v2);
+                const T E = v2 * half_m_over_e;
                 acc[0] += x; acc[1] += y; acc[2] += z;
                 acc[3] += x * x; acc[4] += y * y; acc[5] += z * z;
                 acc[6] += v;
                 acc[7] += E >= e_ion ? v : T(0);
-                atomicAdd(&s_hist[energy_bin<T>(E)], 1u);
+                atomicAdd(&hsub[M::ebin(E)], 1u);
             };
-            uint32_t nsec = 0u;
-            for (uint32_t q = c0; q < c1; ++q) {
-                T x = svx[q], y = svy[q], z = svz[q];
-                if (do_neut && sw[q] == 1) {
+            if (do_neut && s_misc[2] > 0u) {
+                for (uint32_t w = tid; w < nw; w += NT) s_cmask[w] = s_imask[w];
+                __syncthreads();
+                for_each_masked<NT>(s_cmask, nw, s_list, s_scan, [&](uint32_t q) {
                     const uint32_t l = sl[q];
-                    const T E = T(0.5) * (x * x + y * y + z * z) / e_over_m;
+                    const uint32_t rank = ion_base + s_ioff[q >> 5] + (uint32_t)__popc(s_imask[q >> 5] & ((1u << (q & 31u)) - 1u));
+                    const T x = svx[q], y = svy[q], z = svz[q];
+                    const T E = (x * x + y * y + z * z) * half_m_over_e;
                     const uint4 sc = draw(k0, k1, l, step, TAG_SCATTER);
                     const uint4 sd = draw(k0, k1, l, step, TAG_SECONDARY);
                     const T Ep = E - e_ion;
                     const T Es = unif<T>(sc.z) * Ep;
-                    const T vp = sqrt(T(2) * (Ep - Es) * e_over_m), vs = sqrt(T(2) * Es * e_over_m);
+                    const T vp = M::sqrt(two_e_over_m * (Ep - Es)), vs = M::sqrt(two_e_over_m * Es);
                     T dx, dy, dz, ex2, ey2, ez2;
                     iso_dir<T>(sc.x, sc.y, dx, dy, dz);
                     iso_dir<T>(sd.x, sd.y, ex2, ey2, ez2);
-                    x = vp * dx; y = vp * dy; z = vp * dz;
-                    svx[q] = x; svy[q] = y; svz[q] = z;
+                    svx[q] = vp * dx; svy[q] = vp * dy; svz[q] = vp * dz;
                     const T sx = vs * ex2, sy = vs * ey2, sz = vs * ez2;
-                    const uint32_t slot = s + ion_base + nsec;
-                    ++nsec;
+                    const uint32_t slot = s + rank;
                     a.stage_l[slot] = l;
                     a.stage_vx[slot] = sx; a.stage_vy[slot] = sy; a.stage_vz[slot] = sz;
                     accum(sx, sy, sz);
-                }
-                accum(x, y, z);
+                });
             }
+            for (uint32_t q = tid; q < nloc; q += NT) accum(svx[q], svy[q], svz[q]);
             cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
             if (r == 0 && tid < (unsigned)NBIN) {
                 uint32_t h = 0u;
-                for (unsigned q = 0; q < (unsigned)C; ++q) h += *Cl<C>::at(&s_hist[tid], q);
+                for (unsigned q = 0; q < (unsigned)C; ++q) {
+                    const uint32_t* hq = Cl<C>::at(s_hist, q);
+                    h += hq[tid] + hq[NBIN + tid] + hq[2 * NBIN + tid] + hq[3 * NBIN + tid];
+                }
                 a.hist[(size_t)j * NBIN + tid] = h;
             }
             if (r == 0 && tid == 0) {
@@ -611,20 +763,23 @@ __global__ void __launch_bounds__(NT) k_cells(CellArgs<T> a)
             }
         }
 
+        pc.mark(9);
         // ---- 6. write velocities back through the id list (coalesced)
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
             if (k < nh) {
                 const uint32_t pos = hp[i] & 0xFFFFu, l = hl[i];
-                const uint32_t o = pos_owner(pos, n, C);
-                const uint32_t lp = pos - pos_begin(o, n, C);
+                uint32_t p0;
+                const uint32_t o = PB.locate(pos, p0);
+                const uint32_t lp = pos - p0;
                 a.vx[l] = *Cl<C>::at(svx + lp, o);
                 a.vy[l] = *Cl<C>::at(svy + lp, o);
                 a.vz[l] = *Cl<C>::at(svz + lp, o);
             }
         }
         Cl<C>::sync();
+        pc.mark(10);
     }
 }
 

@@ -10,6 +10,9 @@ static const CellKernelEntry kF64[] = {
     CellKernel<double, 4, 256, 12>::entry(),  // 2: <= 12288
     CellKernel<double, 8, 256, 16>::entry(),  // 3: <= 32768
     CellKernel<double, 8, 512, 12>::entry(),  // 4: <= 49152
+    CellKernel<double, 1, 512, 8>::entry(),   // 5: <= 4096
+    CellKernel<double, 1, 1024, 6>::entry(),  // 6: <= 6144, one CTA per cell
+    CellKernel<double, 2, 1024, 6>::entry(),  // 7: <= 12288
 };
 
 int cell_kernels_f64(const CellKernelEntry** out)

@@ -175,6 +175,7 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.e_ion = ctx->cfg.e_ion;
     a.mratio2 = ctx->cfg.mass_neutral > 0 ? 2.0 * ctx->cfg.mass / ctx->cfg.mass_neutral : 0.0;
     a.order_out = nullptr;
+    a.phase_clk = nullptr;
     return a;
 }
 
@@ -182,7 +183,7 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
 // bookkeeping that appends secondaries and regroups for the next pass.
 template <class T>
 int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out, cudaStream_t s,
-                 cudaEvent_t* ev = nullptr)
+                 cudaEvent_t* ev = nullptr, unsigned long long* phase_clk = nullptr)
 {
     const Layout& L = ctx->L;
     const int grid_stream = ctx->sms * 8;
@@ -194,6 +195,7 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
     CK(mark());
     CellArgs<T> a = make_args<T>(ctx, flags);
     a.order_out = order_out;
+    a.phase_clk = phase_clk;
     for (int k = 0; k < ctx->lists.n_classes; ++k) {
         a.list = ctx->lists.list[k];
         a.cls = (uint32_t)k;
@@ -217,11 +219,11 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
 }
 
 int enqueue(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out = nullptr, cudaStream_t s = nullptr,
-            cudaEvent_t* ev = nullptr)
+            cudaEvent_t* ev = nullptr, unsigned long long* phase_clk = nullptr)
 {
     if (!s) s = ctx->stream;
-    return ctx->cfg.precision == LTPC_F32 ? enqueue_pass<float>(ctx, flags, advance, order_out, s, ev)
-                                          : enqueue_pass<double>(ctx, flags, advance, order_out, s, ev);
+    return ctx->cfg.precision == LTPC_F32 ? enqueue_pass<float>(ctx, flags, advance, order_out, s, ev, phase_clk)
+                                          : enqueue_pass<double>(ctx, flags, advance, order_out, s, ev, phase_clk);
 }
 
 int set_state(ltpc_ctx* ctx, int64_t step, double dt)
@@ -279,12 +281,13 @@ int read_errors(ltpc_ctx* ctx)
 // Class tables: index lists into the compiled shapes of each precision.
 namespace ltpc {
 static const ClassTable kTabF32[] = {
-    {5, {0, 1, 2, 3, 4}},   // small CTAs (256 threads), clusters of 1/2/4/8
-    {3, {5, 2, 4}},         // 512-thread CTAs for cells <= 4096, then clusters
-    {2, {6, 4}},            // one 1024-thread CTA per cell up to 12288
+    {5, {0, 5, 6, 3, 4}},   // one CTA per cell up to 12288 (256/512/1024 threads), then clusters of 8
+    {5, {0, 1, 2, 3, 4}},   // 256-thread CTAs in clusters of 1/2/4/8
+    {2, {6, 4}},            // one 1024-thread CTA per cell up to 12288, then clusters of 8
 };
 static const ClassTable kTabF64[] = {
-    {5, {0, 1, 2, 3, 4}},
+    {6, {0, 5, 6, 7, 3, 4}},   // one CTA per cell up to 6144, then clusters of 2/8
+    {5, {0, 1, 2, 3, 4}},      // 256-thread CTAs in clusters of 1/2/4/8
 };
 int class_tables(int precision, const ClassTable** out)
 {
@@ -487,6 +490,17 @@ int ltpc_profile_step(ltpc_ctx* ctx, double dt, int64_t step, float* ms, int32_t
     }
     for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
     *n_out = nk;
+    return rc;
+}
+
+int ltpc_profile_phases(ltpc_ctx* ctx, double dt, int64_t step, unsigned long long* d_cycles)
+{
+    if (!ctx || !d_cycles) return LTPC_EINVAL;
+    CK(cudaMemsetAsync(d_cycles, 0, 16 * sizeof(unsigned long long), ctx->stream));
+    int rc = set_state(ctx, step, dt);
+    if (rc == LTPC_OK) rc = enqueue(ctx, step_flags(ctx, true, true), true, nullptr, ctx->stream, nullptr, d_cycles);
+    ctx->next_step = step + 1;
+    ctx->cur_dt = dt;
     return rc;
 }
 

@@ -7,7 +7,8 @@
 //                     the CTA loads these particles' ids and velocities
 //                     (coalesced) and writes them back at the end.
 //   * bucket ranges : sort buckets [B(r), B(r+1)), B(r) = floor(r nb / C),
-//                     nb = ceil(n / 4); the CTA keeps those bucket counters.
+//                     nb = n (one bucket per particle on average); the CTA
+//                     keeps those bucket counters.
 //   * pair slots    : slots [Q(r), Q(r+1)), Q(r) = floor(r half / C),
 //                     half = ceil(n / 2); slot p covers pairing-order
 //                     positions 2p and 2p+1, so the CTA owns positions
@@ -36,7 +37,7 @@ LTPC_HD uint32_t split_owner(uint32_t t, uint32_t total, uint32_t C)
     return (uint32_t)((((uint64_t)t + 1u) * C - 1u) / total);
 }
 
-LTPC_HD uint32_t n_buckets(uint32_t n) { return n < 4 ? 1u : (n + 3u) / 4u; }
+LTPC_HD uint32_t n_buckets(uint32_t n) { return n < 1 ? 1u : n; }
 LTPC_HD uint32_t n_half(uint32_t n) { return (n + 1u) / 2u; }
 
 // First pairing-order position owned by CTA r.

@@ -64,6 +64,7 @@ struct CellArgs {
     double weight, mass, e_over_m;
     double n_neutral, sigma_el, sigma_ion, e_ion, mratio2;  // mratio2 = 2 m / M
     uint32_t* order_out;         // optional: pairing order written at I_j + position
+    unsigned long long* phase_clk; // optional: SM cycles spent per kernel phase (tracing)
 };
 
 }  // namespace ltpc

@@ -67,6 +67,7 @@ def load_library(path: str = LIB_PATH):
             "ltpc_step": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_run": (C.c_int, [vp, C.c_double, i64, i64]),
             "ltpc_profile_step": (C.c_int, [vp, C.c_double, i64, C.POINTER(C.c_float), i32, C.POINTER(i32)]),
+            "ltpc_profile_phases": (C.c_int, [vp, C.c_double, i64, vp]),
             "ltpc_moments": (C.c_int, [vp, vp, vp, C.c_int]),
             "ltpc_read_particles": (C.c_int, [vp, vp, vp, vp, vp, vp, C.POINTER(i64), C.c_int]),
             "ltpc_sync": (C.c_int, [vp]),
@@ -230,6 +231,18 @@ class Collider:
         n = C.c_int32()
         self._check(self.L.ltpc_profile_step(self.ctx, float(dt), int(step), ms, 16, C.byref(n)), "profile_step")
         return [ms[k] for k in range(n.value)]
+
+    PHASES = ["fetch", "keys", "bucket_scan", "place", "rank", "pos_lookup", "gather", "coulomb", "neutral",
+              "moments", "writeback"]
+
+    def profile_phases(self, dt, step):
+        """SM cycles per cell-kernel phase (summed over CTAs) for one step."""
+        t = self.torch
+        buf = t.zeros(16, dtype=t.int64, device=self.device)
+        self._check(self.L.ltpc_profile_phases(self.ctx, float(dt), int(step), _ptr(buf)), "profile_phases")
+        self.sync()
+        v = buf.cpu().numpy()
+        return dict(zip(self.PHASES, v[:len(self.PHASES)].tolist()))
 
     def sync(self):
         self._check(self.L.ltpc_sync(self.ctx), "sync")

@@ -30,7 +30,7 @@ int main(int argc, char** argv) {
                 unsigned hb = split_begin(r, n, C), he = split_begin(r + 1, n, C);
                 if (he - hb > capl) return fail("home > capl", n, C, r);
                 unsigned bb = split_begin(r, nb, C), be = split_begin(r + 1, nb, C);
-                if (be - bb > capl / 4 + 2) return fail("buckets > capl/4+2", n, C, r);
+                if (be - bb > capl) return fail("buckets > capl", n, C, r);
             }
             if (prev_end != n) return fail("pos cover", n, C, prev_end);
             for (unsigned q = 0; q < n; ++q) {
