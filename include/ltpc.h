@@ -182,6 +182,30 @@ int ltpc_classes(ltpc_ctx* ctx, int32_t* n_classes, int32_t* cluster, int32_t* t
 int ltpc_autotune(ltpc_ctx* ctx, double dt, int32_t* chosen_table);
 int ltpc_set_class_table(ltpc_ctx* ctx, int32_t table);
 
+/* Largest number of cells ltpc_group_cells_noalloc accepts. */
+#define LTPC_NOALLOC_MAX_CELLS 131072
+
+/* Grouping of particle ids by cell (counts, start offsets and the index list
+ * of ltpc_grouping) for callers that cannot allocate device memory: code
+ * inside a program whose memory pool owns the whole device, code whose device
+ * budget is already reserved, or a loop that must not pay for an allocation.
+ * The paper has no counterpart; it is a service of this library.
+ * Inputs: d_cell[n] (device int32 cell ids).  Outputs: d_cell_start[n_cells+1]
+ * and d_perm[n] (device uint32): d_perm[d_cell_start[j] ..
+ * d_cell_start[j+1]) holds the ids of cell j's particles (order inside a cell
+ * unspecified).  The per-cell counters live in a fixed device array of this
+ * library (LTPC_NOALLOC_MAX_CELLS + 64 words on every GPU that loads it, kept
+ * until exit); no cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make the first call on each device before any
+ * stream capture.  Every call shares the array and clears what it uses; calls
+ * whose work overlaps on the GPU race.  Synchronizes `cuda_stream` (a
+ * cudaStream_t, NULL = legacy default stream).  Errors: EINVAL (n < 0,
+ * n_cells outside [1, LTPC_NOALLOC_MAX_CELLS], a NULL buffer, or a cell id
+ * outside [0, n_cells)), ECUDA. */
+int ltpc_group_cells_noalloc(const int32_t* d_cell, int64_t n, int32_t n_cells, uint32_t* d_cell_start,
+                             uint32_t* d_perm, void* cuda_stream);
+
 /* Short text for a status code (static storage). */
 const char* ltpc_strerror(int code);
 

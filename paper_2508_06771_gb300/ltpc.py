@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
                                        C.POINTER(i32)]),
             "ltpc_autotune": (C.c_int, [vp, C.c_double, C.POINTER(i32)]),
             "ltpc_set_class_table": (C.c_int, [vp, i32]),
+            "ltpc_group_cells_noalloc": (C.c_int, [vp, i64, i32, vp, vp, vp]),
             "ltpc_strerror": (C.c_char_p, [C.c_int]),
             "ltpc_last_cuda_error": (C.c_char_p, [vp]),
         }
@@ -318,6 +319,29 @@ class Collider:
         ch = C.c_int32()
         self._check(self.L.ltpc_autotune(self.ctx, float(dt), C.byref(ch)), "autotune")
         return ch.value
+
+
+NOALLOC_MAX_CELLS = 131072
+
+
+def group_cells_noalloc(cell, n_cells: int, stream=None):
+    """Group particle ids by cell without any device allocation by the library.
+
+    For callers that may not allocate device memory themselves (the library keeps
+    its counters in a fixed device array).  ``cell`` is a CUDA int32 tensor; the
+    outputs are allocated here by the caller side (torch) and returned as
+    (cell_start[n_cells + 1], perm[n]) uint32 numpy arrays.  Raises LtpcError.
+    """
+    import torch
+    L = load_library()
+    n = int(cell.numel())
+    cs = torch.empty(n_cells + 1, dtype=torch.int32, device=cell.device)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=cell.device)
+    st = stream if stream is not None else torch.cuda.current_stream(cell.device)
+    rc = L.ltpc_group_cells_noalloc(_ptr(cell), n, int(n_cells), _ptr(cs), _ptr(perm), st.cuda_stream)
+    if rc != OK:
+        raise LtpcError(rc, "group_cells_noalloc")
+    return cs.cpu().numpy().view(np.uint32), perm[:n].cpu().numpy().view(np.uint32)
 
 
 def header_symbols(header: str | None = None):
