@@ -182,6 +182,54 @@ int ltpc_classes(ltpc_ctx* ctx, int32_t* n_classes, int32_t* cluster, int32_t* t
 int ltpc_autotune(ltpc_ctx* ctx, double dt, int32_t* chosen_table);
 int ltpc_set_class_table(ltpc_ctx* ctx, int32_t table);
 
+/* ---- rate-coefficient surrogate --------------------------------------------
+ * A perceptron 66 -> 128 -> 128 -> 2 with GELU that maps a cell's energy
+ * distribution to its ionization and elastic rate coefficients
+ * k_c = sum sigma_c |v| / N (the C_kc terms of Eq. 1 per electron; Sec. 1
+ * motivates resolving the distribution's tail).  Inputs per cell (66): the 64
+ * histogram fractions of ltpc_moments, log10 n_e and the mean energy [eV],
+ * normalised as (x - mean) / std; outputs: k_ion / scale_0, k_el / scale_1.
+ * Weights and activations are bfloat16 with FP32 accumulation (tensor-core
+ * MMAs); master weights, biases and Adam moments are FP32.  Parameters are
+ * packed as W1 [128][80] (input columns 66..79 zero), b1 [128], W2
+ * [128][128], b2 [128], W3 [2][128], b3 [2] (ltpc_mlp_param_count floats).
+ * Device arrays X [B][66], T and Y [B][2] are float, row-major.  All calls
+ * run on the stream given at creation unless stated; errors as above. */
+typedef struct ltpc_mlp ltpc_mlp;
+int ltpc_mlp_param_count(void);
+/* Bytes of the caller-owned device buffer for batches of up to batch_max rows
+ * and up to n_cells_max cells in the context-coupled calls. */
+int ltpc_mlp_required_bytes(int32_t batch_max, int32_t n_cells_max, size_t* bytes);
+/* Create with deterministic initial weights (uniform +-1/sqrt(fan_in) from
+ * Philox with `seed`); d_buf 256-byte aligned.  Synchronizing. */
+int ltpc_mlp_create(ltpc_mlp** out, void* d_buf, int32_t batch_max, int32_t n_cells_max, uint64_t seed,
+                    void* cuda_stream);
+void ltpc_mlp_destroy(ltpc_mlp* mlp);
+int ltpc_mlp_set_params(ltpc_mlp* mlp, const float* params, int src_is_device);   /* synchronizing */
+int ltpc_mlp_get_params(ltpc_mlp* mlp, float* params, int dst_is_device);         /* synchronizing */
+/* Feature means and standard deviations [66] and target scales [2] (host). */
+int ltpc_mlp_set_norm(ltpc_mlp* mlp, const float* feat_mean, const float* feat_std, const float* target_scale);
+/* Y = network(X) for B <= batch_max rows. */
+int ltpc_mlp_forward(ltpc_mlp* mlp, const float* d_X, int32_t B, float* d_Y);
+/* Mean-squared-error loss of (X, T) and its gradient w.r.t. every parameter
+ * (packed order) into d_grad (may be NULL) and d_loss (may be NULL). */
+int ltpc_mlp_gradients(ltpc_mlp* mlp, const float* d_X, const float* d_T, int32_t B, float* d_grad, float* d_loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on (X, T). */
+int ltpc_mlp_train_step(ltpc_mlp* mlp, const float* d_X, const float* d_T, int32_t B, float lr, float* d_loss);
+/* Features [M][66] of every cell of `ctx` from its last moments (normalised
+ * when `normalize`), and the exact rates [M][2] (k_ion, k_el) if d_T != NULL.
+ * Runs on the context's stream. */
+int ltpc_mlp_features(ltpc_ctx* ctx, ltpc_mlp* mlp, float* d_X, float* d_T, int normalize);
+/* In-loop serving: rates [M][2] (k_ion, k_el in m^3/s) predicted for every
+ * cell of `ctx` from its last moments.  Runs on the context's stream. */
+int ltpc_mlp_infer(ltpc_ctx* ctx, ltpc_mlp* mlp, float* d_rates);
+/* Features [M][66] (normalised) of a random subsample of about per_cell
+ * particles of every cell (salt selects the sample) and the direct rate
+ * estimate [M][2] of that subsample; the density feature is the whole
+ * cell's.  Synchronizing. */
+int ltpc_mlp_subsample_features(ltpc_ctx* ctx, ltpc_mlp* mlp, int32_t per_cell, uint32_t salt, float* d_X,
+                                float* d_rates_direct);
+
 /* Largest number of cells ltpc_group_cells_noalloc accepts. */
 #define LTPC_NOALLOC_MAX_CELLS 131072
 

@@ -622,6 +622,38 @@ int ltpc_set_class_table(ltpc_ctx* ctx, int32_t table)
     return read_errors(ctx);
 }
 
+// Views used by the surrogate (k_mlp.cu); not part of the public header.
+int ltpc_internal_moments_view(ltpc_ctx* ctx, const double** mom, const uint32_t** hist, const double** inv_vol,
+                               int32_t* M, double* weight, double* half_m_over_e, cudaStream_t* stream)
+{
+    if (!ctx) return LTPC_EINVAL;
+    *mom = ctx->w<double>(ctx->L.mom);
+    *hist = ctx->w<uint32_t>(ctx->L.hist);
+    *inv_vol = ctx->w<double>(ctx->L.inv_vol);
+    *M = ctx->cfg.n_cells;
+    *weight = ctx->cfg.weight;
+    *half_m_over_e = 0.5 * ctx->cfg.mass / ctx->cfg.charge;
+    *stream = ctx->stream;
+    return LTPC_OK;
+}
+
+int ltpc_internal_particles_view(ltpc_ctx* ctx, const void** vx, const void** vy, const void** vz, const int32_t** cell,
+                                 const uint32_t** counts, unsigned long long* n, int* precision, uint64_t* seed,
+                                 double* sig_el, double* sig_ion, double* e_ion)
+{
+    if (!ctx) return LTPC_EINVAL;
+    int rc = read_errors(ctx);
+    if (rc) return rc;
+    if (cudaMemcpy(n, &ctx->ds->n, sizeof *n, cudaMemcpyDeviceToHost) != cudaSuccess) return LTPC_ECUDA;
+    *vx = ctx->st + ctx->L.vx; *vy = ctx->st + ctx->L.vy; *vz = ctx->st + ctx->L.vz;
+    *cell = ctx->s<int32_t>(ctx->L.cell);
+    *counts = ctx->w<uint32_t>(ctx->L.counts);
+    *precision = ctx->cfg.precision;
+    *seed = ctx->cfg.seed;
+    *sig_el = ctx->cfg.sigma_el; *sig_ion = ctx->cfg.sigma_ion; *e_ion = ctx->cfg.e_ion;
+    return LTPC_OK;
+}
+
 int ltpc_autotune(ltpc_ctx* ctx, double dt, int32_t* chosen_table)
 {
     (void)dt;

@@ -78,6 +78,19 @@ def load_library(path: str = LIB_PATH):
             "ltpc_autotune": (C.c_int, [vp, C.c_double, C.POINTER(i32)]),
             "ltpc_set_class_table": (C.c_int, [vp, i32]),
             "ltpc_group_cells_noalloc": (C.c_int, [vp, i64, i32, vp, vp, vp]),
+            "ltpc_mlp_param_count": (C.c_int, []),
+            "ltpc_mlp_required_bytes": (C.c_int, [i32, i32, C.POINTER(C.c_size_t)]),
+            "ltpc_mlp_create": (C.c_int, [C.POINTER(vp), vp, i32, i32, C.c_uint64, vp]),
+            "ltpc_mlp_destroy": (None, [vp]),
+            "ltpc_mlp_set_params": (C.c_int, [vp, vp, C.c_int]),
+            "ltpc_mlp_get_params": (C.c_int, [vp, vp, C.c_int]),
+            "ltpc_mlp_set_norm": (C.c_int, [vp, vp, vp, vp]),
+            "ltpc_mlp_forward": (C.c_int, [vp, vp, i32, vp]),
+            "ltpc_mlp_gradients": (C.c_int, [vp, vp, vp, i32, vp, vp]),
+            "ltpc_mlp_train_step": (C.c_int, [vp, vp, vp, i32, C.c_float, vp]),
+            "ltpc_mlp_features": (C.c_int, [vp, vp, vp, vp, C.c_int]),
+            "ltpc_mlp_infer": (C.c_int, [vp, vp, vp]),
+            "ltpc_mlp_subsample_features": (C.c_int, [vp, vp, i32, C.c_uint32, vp, vp]),
             "ltpc_strerror": (C.c_char_p, [C.c_int]),
             "ltpc_last_cuda_error": (C.c_char_p, [vp]),
         }
@@ -319,6 +332,112 @@ class Collider:
         ch = C.c_int32()
         self._check(self.L.ltpc_autotune(self.ctx, float(dt), C.byref(ch)), "autotune")
         return ch.value
+
+
+class Surrogate:
+    """Rate-coefficient network (see include/ltpc.h): features -> (k_ion, k_el)."""
+
+    DIN, H, DOUT = 66, 128, 2
+
+    def __init__(self, batch_max=4096, n_cells_max=4096, seed=0, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.L = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.batch_max = int(batch_max)
+        nb = C.c_size_t()
+        rc = self.L.ltpc_mlp_required_bytes(self.batch_max, int(n_cells_max), C.byref(nb))
+        if rc != OK:
+            raise LtpcError(rc, "mlp_required_bytes")
+        self.buf = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        rc = self.L.ltpc_mlp_create(C.byref(h), _ptr(self.buf), self.batch_max, int(n_cells_max), int(seed),
+                                    self.stream.cuda_stream)
+        if rc != OK:
+            raise LtpcError(rc, "mlp_create")
+        self.h = h
+        self.nparam = int(self.L.ltpc_mlp_param_count())
+        self.loss_buf = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def _chk(self, rc, where):
+        if rc != OK:
+            raise LtpcError(rc, where)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ltpc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # packed parameter vector <-> dict of float64 arrays (oracle layout: W1 [128][66])
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparam, np.float32)
+        self._chk(self.L.ltpc_mlp_get_params(self.h, out.ctypes.data, 0), "mlp_get_params")
+        return out
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._chk(self.L.ltpc_mlp_set_params(self.h, flat.ctypes.data, 0), "mlp_set_params")
+
+    def unpack(self, flat):
+        H, D = self.H, self.DIN
+        o = 0
+        W1 = flat[o:o + H * 80].reshape(H, 80)[:, :D]; o += H * 80
+        b1 = flat[o:o + H]; o += H
+        W2 = flat[o:o + H * H].reshape(H, H); o += H * H
+        b2 = flat[o:o + H]; o += H
+        W3 = flat[o:o + 2 * H].reshape(2, H); o += 2 * H
+        b3 = flat[o:o + 2]
+        return {k: np.asarray(v, np.float64) for k, v in
+                dict(W1=W1, b1=b1, W2=W2, b2=b2, W3=W3, b3=b3).items()}
+
+    def set_norm(self, mean, std, tscale):
+        m = np.ascontiguousarray(mean, np.float32)
+        s_ = np.ascontiguousarray(std, np.float32)
+        t = np.ascontiguousarray(tscale, np.float32)
+        self._chk(self.L.ltpc_mlp_set_norm(self.h, m.ctypes.data, s_.ctypes.data, t.ctypes.data), "mlp_set_norm")
+        self.norm = (m, s_, t)
+
+    def forward(self, X):
+        B = int(X.shape[0])
+        Y = self.torch.empty((B, 2), dtype=self.torch.float32, device=self.device)
+        self._chk(self.L.ltpc_mlp_forward(self.h, _ptr(X), B, _ptr(Y)), "mlp_forward")
+        return Y
+
+    def gradients(self, X, T):
+        g = self.torch.empty(self.nparam, dtype=self.torch.float32, device=self.device)
+        self._chk(self.L.ltpc_mlp_gradients(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(g), _ptr(self.loss_buf)),
+                  "mlp_gradients")
+        return g, self.loss_buf
+
+    def train_step(self, X, T, lr=1e-3):
+        self._chk(self.L.ltpc_mlp_train_step(self.h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),
+                                             _ptr(self.loss_buf)), "mlp_train_step")
+        return self.loss_buf
+
+    def features(self, col, normalize=True):
+        X = self.torch.empty((col.M, 66), dtype=self.torch.float32, device=self.device)
+        T = self.torch.empty((col.M, 2), dtype=self.torch.float32, device=self.device)
+        self._chk(self.L.ltpc_mlp_features(col.ctx, self.h, _ptr(X), _ptr(T), int(bool(normalize))), "mlp_features")
+        return X, T
+
+    def subsample_features(self, col, per_cell, salt):
+        X = self.torch.empty((col.M, 66), dtype=self.torch.float32, device=self.device)
+        R = self.torch.empty((col.M, 2), dtype=self.torch.float32, device=self.device)
+        self._chk(self.L.ltpc_mlp_subsample_features(col.ctx, self.h, int(per_cell), int(salt) & 0xFFFFFFFF,
+                                                     _ptr(X), _ptr(R)), "mlp_subsample_features")
+        return X, R
+
+    def infer(self, col, out=None):
+        R = out if out is not None else self.torch.empty((col.M, 2), dtype=self.torch.float32, device=self.device)
+        self._chk(self.L.ltpc_mlp_infer(col.ctx, self.h, _ptr(R)), "mlp_infer")
+        return R
 
 
 NOALLOC_MAX_CELLS = 131072
