@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // through a bit mask so that whole warps redraw and collide them.
         const uint32_t nw = (nloc + 31u) / 32u;
         uint32_t ion_base = 0u;      // secondaries of lower-ranked CTAs of this cell
-        const T half_m_over_e = (T)(0.5 / a.e_over_m);
+        const T half_m_over_e = a.c_half_m_over_e;
         if (do_neut) {
             const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl);
             if (tid == 0) {   // null-collision bound of the cell, in the working precision
@@ -656,8 +656,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 if ((tid & 31u) == 0u && q0 + tid < nloc + 31u) s_cmask[(q0 + tid) >> 5] = m;
             }
             __syncthreads();
-            const T nsel = (T)(a.n_neutral * a.sigma_el), nsion = (T)(a.n_neutral * a.sigma_ion);
-            const T e_ion = (T)a.e_ion, mr2 = (T)a.mratio2;
+            const T nsel = a.c_nsig_el, nsion = a.c_nsig_ion;
+            const T e_ion = a.c_e_ion, mr2 = a.c_mratio2;
             for_each_masked<NT>(s_cmask, nw, s_list, s_scan, [&](uint32_t q) {
                 const uint32_t l = sl[q];
                 const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // ---- 5. ionization outcomes (C2), then the moments (S3a/S3b) of the cell
         {
             using M = Math<T>;
-            const T e_ion = (T)a.e_ion, two_e_over_m = (T)(2.0 * a.e_over_m);
+            const T e_ion = a.c_e_ion, two_e_over_m = a.c_two_e_over_m;
             T acc[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[k] = T(0);

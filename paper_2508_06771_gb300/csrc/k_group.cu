@@ -29,22 +29,41 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
 }
 
 // CCS3: perm[I_j + rank] = l with one atomic cursor update per warp and cell.
+// Each thread handles SCATTER_ILP particles per iteration so that their
+// cursor atomics are in flight together instead of one round trip at a time.
+constexpr int SCATTER_ILP = 4;
+
 static __global__ void k_scatter(const int32_t* __restrict__ cell, uint32_t* __restrict__ cursor,
-                          uint32_t* __restrict__ perm, const DevState* __restrict__ ds)
+                                 uint32_t* __restrict__ perm, const DevState* __restrict__ ds)
 {
     const unsigned long long n = ds->n;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned lane = threadIdx.x & 31u;
-    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += stride) {
-        const int32_t c = cell[l];
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, c);
-        const unsigned leader = __ffs(peers) - 1;
-        uint32_t base = 0u;
-        if (lane == leader) base = atomicAdd(&cursor[c], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-        perm[base + rank] = (uint32_t)l;
+    for (unsigned long long l0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l0 < n;
+         l0 += stride * SCATTER_ILP) {
+        int32_t c[SCATTER_ILP];
+#pragma unroll
+        for (int u = 0; u < SCATTER_ILP; ++u) {
+            const unsigned long long l = l0 + u * stride;
+            c[u] = l < n ? cell[l] : -1;
+        }
+        uint32_t base[SCATTER_ILP], rank[SCATTER_ILP];
+        unsigned peers[SCATTER_ILP];
+#pragma unroll
+        for (int u = 0; u < SCATTER_ILP; ++u) {
+            const unsigned act = __activemask();
+            peers[u] = __match_any_sync(act, c[u]);
+            const unsigned leader = __ffs(peers[u]) - 1;
+            base[u] = 0u;
+            if (lane == leader && c[u] >= 0) base[u] = atomicAdd(&cursor[c[u]], (uint32_t)__popc(peers[u]));
+            rank[u] = __popc(peers[u] & ((1u << lane) - 1u));
+        }
+#pragma unroll
+        for (int u = 0; u < SCATTER_ILP; ++u) {
+            const unsigned leader = __ffs(peers[u]) - 1;
+            const uint32_t b = __shfl_sync(peers[u], base[u], leader);
+            if (c[u] >= 0) perm[b + rank[u]] = (uint32_t)(l0 + u * stride);
+        }
     }
 }
 

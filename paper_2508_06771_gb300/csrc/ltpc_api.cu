@@ -174,6 +174,12 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.sigma_ion = ctx->cfg.sigma_ion;
     a.e_ion = ctx->cfg.e_ion;
     a.mratio2 = ctx->cfg.mass_neutral > 0 ? 2.0 * ctx->cfg.mass / ctx->cfg.mass_neutral : 0.0;
+    a.c_half_m_over_e = (T)(0.5 * ctx->cfg.mass / ctx->cfg.charge);
+    a.c_two_e_over_m = (T)(2.0 * ctx->cfg.charge / ctx->cfg.mass);
+    a.c_nsig_el = (T)(ctx->cfg.n_neutral * ctx->cfg.sigma_el);
+    a.c_nsig_ion = (T)(ctx->cfg.n_neutral * ctx->cfg.sigma_ion);
+    a.c_e_ion = (T)ctx->cfg.e_ion;
+    a.c_mratio2 = (T)a.mratio2;
     a.order_out = nullptr;
     a.phase_clk = nullptr;
     return a;

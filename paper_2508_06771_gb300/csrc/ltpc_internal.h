@@ -63,6 +63,11 @@ struct CellArgs {
     double coef0;                // q^4 w / (8 pi eps0^2 mu^2), mu = m/2
     double weight, mass, e_over_m;
     double n_neutral, sigma_el, sigma_ion, e_ion, mratio2;  // mratio2 = 2 m / M
+    // the same constants in the working precision (computed on the host)
+    T c_half_m_over_e;           // m / (2 e): squared speed -> energy in eV
+    T c_two_e_over_m;            // 2 e / m: energy in eV -> squared speed
+    T c_nsig_el, c_nsig_ion;     // n_n sigma_el, n_n sigma_ion
+    T c_e_ion, c_mratio2;
     uint32_t* order_out;         // optional: pairing order written at I_j + position
     unsigned long long* phase_clk; // optional: SM cycles spent per kernel phase (tracing)
 };
