@@ -12,6 +12,7 @@ static const CellKernelEntry kF32[] = {
     CellKernel<float, 8, 512, 16>::entry(),   // 4: <= 65536
     CellKernel<float, 1, 512, 8>::entry(),    // 5: <= 4096
     CellKernel<float, 1, 1024, 12>::entry(),  // 6: <= 12288, one CTA per cell
+    CellKernel<float, 1, 512, 24>::entry(),   // 7: <= 12288, one 512-thread CTA per cell
 };
 
 int cell_kernels_f32(const CellKernelEntry** out)

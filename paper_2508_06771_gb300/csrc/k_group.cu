@@ -28,41 +28,49 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
     }
 }
 
-// CCS3: perm[I_j + rank] = l with one atomic cursor update per warp and cell.
-// Each thread handles SCATTER_ILP particles per iteration so that their
-// cursor atomics are in flight together instead of one round trip at a time.
-constexpr int SCATTER_ILP = 4;
-
+// CCS3: perm[I_j + rank] = l.  Each warp takes 128 consecutive particles (4 per
+// lane, 16-byte loads).  When they all belong to one cell -- the usual case for
+// cell-grouped storage -- one cursor atomic serves the 128 and the ids are
+// written with 16-byte stores; otherwise one atomic per warp and cell.
 static __global__ void k_scatter(const int32_t* __restrict__ cell, uint32_t* __restrict__ cursor,
                                  uint32_t* __restrict__ perm, const DevState* __restrict__ ds)
 {
     const unsigned long long n = ds->n;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const unsigned lane = threadIdx.x & 31u;
-    for (unsigned long long l0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l0 < n;
-         l0 += stride * SCATTER_ILP) {
-        int32_t c[SCATTER_ILP];
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long w0 = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (unsigned long long base = w0 * 128ull; base < n; base += nwarps * 128ull) {
+        const unsigned long long l0 = base + 4ull * lane;
+        int32_t c[4];
+        if (l0 + 3 < n) {
+            const int4 v = *reinterpret_cast<const int4*>(cell + l0);
+            c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+        } else {
 #pragma unroll
-        for (int u = 0; u < SCATTER_ILP; ++u) {
-            const unsigned long long l = l0 + u * stride;
-            c[u] = l < n ? cell[l] : -1;
+            for (int u = 0; u < 4; ++u) c[u] = l0 + u < n ? cell[l0 + u] : -1;
         }
-        uint32_t base[SCATTER_ILP], rank[SCATTER_ILP];
-        unsigned peers[SCATTER_ILP];
-#pragma unroll
-        for (int u = 0; u < SCATTER_ILP; ++u) {
-            const unsigned act = __activemask();
-            peers[u] = __match_any_sync(act, c[u]);
-            const unsigned leader = __ffs(peers[u]) - 1;
-            base[u] = 0u;
-            if (lane == leader && c[u] >= 0) base[u] = atomicAdd(&cursor[c[u]], (uint32_t)__popc(peers[u]));
-            rank[u] = __popc(peers[u] & ((1u << lane) - 1u));
+        const int32_t c0 = __shfl_sync(0xFFFFFFFFu, c[0], 0);
+        const bool same = c[0] == c0 && c[1] == c0 && c[2] == c0 && c[3] == c0;
+        if (__all_sync(0xFFFFFFFFu, same) && c0 >= 0) {           // one cell, 128 particles
+            uint32_t b = 0u;
+            if (lane == 0) b = atomicAdd(&cursor[c0], 128u);
+            b = __shfl_sync(0xFFFFFFFFu, b, 0) + 4u * lane;
+            const uint32_t l = (uint32_t)l0;
+            if ((b & 3u) == 0u) {
+                *reinterpret_cast<uint4*>(perm + b) = make_uint4(l, l + 1u, l + 2u, l + 3u);
+            } else {
+                perm[b] = l; perm[b + 1] = l + 1u; perm[b + 2] = l + 2u; perm[b + 3] = l + 3u;
+            }
+            continue;
         }
 #pragma unroll
-        for (int u = 0; u < SCATTER_ILP; ++u) {
-            const unsigned leader = __ffs(peers[u]) - 1;
-            const uint32_t b = __shfl_sync(peers[u], base[u], leader);
-            if (c[u] >= 0) perm[b + rank[u]] = (uint32_t)(l0 + u * stride);
+        for (int u = 0; u < 4; ++u) {                             // mixed cells
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, c[u]);
+            const unsigned leader = __ffs(peers) - 1;
+            uint32_t b = 0u;
+            if (lane == leader && c[u] >= 0) b = atomicAdd(&cursor[c[u]], (uint32_t)__popc(peers));
+            b = __shfl_sync(0xFFFFFFFFu, b, leader);
+            if (c[u] >= 0) perm[b + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)(l0 + u);
         }
     }
 }

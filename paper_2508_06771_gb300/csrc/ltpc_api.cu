@@ -290,6 +290,7 @@ static const ClassTable kTabF32[] = {
     {5, {0, 5, 6, 3, 4}},   // one CTA per cell up to 12288 (256/512/1024 threads), then clusters of 8
     {5, {0, 1, 2, 3, 4}},   // 256-thread CTAs in clusters of 1/2/4/8
     {2, {6, 4}},            // one 1024-thread CTA per cell up to 12288, then clusters of 8
+    {5, {0, 5, 7, 3, 4}},   // as table 0 with 512-thread CTAs (24 positions per thread) up to 12288
 };
 static const ClassTable kTabF64[] = {
     {6, {0, 5, 6, 7, 3, 4}},   // one CTA per cell up to 6144, then clusters of 2/8
