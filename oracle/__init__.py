@@ -81,8 +81,13 @@ def lib():
             L.orc_nrl_lnlambda.restype = C.c_double
             L.orc_coulomb.argtypes = [C.c_int64, C.c_int32, i32p, f64p, f64p, f64p, f64p, f64p, f64p,
                                       C.POINTER(Params), C.c_uint32]
+            L.orc_coulomb_ids.argtypes = [C.c_int64, C.c_int32, i32p, u32p, f64p, f64p, f64p, f64p, f64p, f64p,
+                                          C.POINTER(Params), C.c_uint32]
+            L.orc_pair_order_ids.argtypes = [C.c_int64, C.c_int32, i32p, u32p, C.c_uint64, C.c_uint32, u64p, u32p]
             L.orc_neutral.argtypes = [i64p, C.c_int64, C.c_int32, i32p, f64p, f64p, f64p, f64p, f64p,
                                       C.POINTER(Params), C.c_uint32, i64p, C.POINTER(C.c_int8), f64p]
+            L.orc_neutral_ids.argtypes = [i64p, C.c_int64, C.c_int32, i32p, u32p, f64p, f64p, f64p, f64p, f64p,
+                                          C.POINTER(Params), C.c_uint32, i64p, C.POINTER(C.c_int8), f64p]
             L.orc_energy_bin.argtypes = [C.c_double]
             L.orc_energy_bin.restype = C.c_int
             L.orc_moments.argtypes = [C.c_int64, C.c_int32, i32p, f64p, f64p, f64p, C.POINTER(Params),
@@ -184,6 +189,7 @@ class State:
         self.x = np.zeros(cap, np.float64)
         if wl.get("x") is not None:
             self.x[:n] = wl["x"]
+        self.ids = None if wl.get("ids") is None else np.ascontiguousarray(wl["ids"], dtype=np.uint32)
         self.inv_vol = np.ascontiguousarray(wl["inv_vol"], dtype=np.float64)
         self.dt = np.ascontiguousarray(wl["dt_cell"], dtype=np.float64)
         self.lnlam = np.ascontiguousarray(wl["lnlam_cell"], dtype=np.float64)
@@ -194,10 +200,12 @@ class State:
 
 
 def coulomb(st: State, params: Params, step: int, lnlam: np.ndarray | None = None):
+    """Step S1 on the oracle state; st.ids (if set) are the particles' random-stream ids."""
     ln = st.lnlam if lnlam is None else np.ascontiguousarray(lnlam, dtype=np.float64)
-    _check(lib().orc_coulomb(st.n, st.M, _p(st.cell, C.c_int32), _p(st.vx, C.c_double),
-                             _p(st.vy, C.c_double), _p(st.vz, C.c_double), _p(st.inv_vol, C.c_double),
-                             _p(ln, C.c_double), _p(st.dt, C.c_double), C.byref(params), step))
+    ids = getattr(st, "ids", None)
+    _check(lib().orc_coulomb_ids(st.n, st.M, _p(st.cell, C.c_int32), _p(ids, C.c_uint32), _p(st.vx, C.c_double),
+                                 _p(st.vy, C.c_double), _p(st.vz, C.c_double), _p(st.inv_vol, C.c_double),
+                                 _p(ln, C.c_double), _p(st.dt, C.c_double), C.byref(params), step))
 
 
 def neutral(st: State, params: Params, step: int, with_decisions: bool = False):
@@ -205,10 +213,11 @@ def neutral(st: State, params: Params, step: int, with_decisions: bool = False):
     counts = np.zeros(3, np.int64)
     dec = np.zeros(max(st.n, 1), np.int8) if with_decisions else None
     mar = np.zeros(max(st.n, 1), np.float64) if with_decisions else None
-    rc = lib().orc_neutral(C.byref(n), st.capacity, st.M, _p(st.cell, C.c_int32), _p(st.x, C.c_double),
-                           _p(st.vx, C.c_double), _p(st.vy, C.c_double), _p(st.vz, C.c_double),
-                           _p(st.dt, C.c_double), C.byref(params), step, _p(counts, C.c_int64),
-                           _p(dec, C.c_int8), _p(mar, C.c_double))
+    ids = getattr(st, "ids", None)
+    rc = lib().orc_neutral_ids(C.byref(n), st.capacity, st.M, _p(st.cell, C.c_int32), _p(ids, C.c_uint32),
+                               _p(st.x, C.c_double), _p(st.vx, C.c_double), _p(st.vy, C.c_double),
+                               _p(st.vz, C.c_double), _p(st.dt, C.c_double), C.byref(params), step,
+                               _p(counts, C.c_int64), _p(dec, C.c_int8), _p(mar, C.c_double))
     if rc == ECAPACITY:
         raise OverflowError("oracle: particle capacity exceeded")
     _check(rc)

@@ -124,16 +124,6 @@ int orc_group(int64_t n, int32_t M, const int32_t *cell,
  * of that order.  This is the per-step re-randomised partner choice the
  * Takizuka-Abe model needs.
  * ------------------------------------------------------------------------- */
-typedef struct { uint32_t key; uint32_t l; } orc_kl;
-
-static int orc_kl_cmp(const void *a, const void *b)
-{
-    const orc_kl *x = (const orc_kl *)a, *y = (const orc_kl *)b;
-    if (x->key != y->key) return x->key < y->key ? -1 : 1;
-    if (x->l != y->l) return x->l < y->l ? -1 : 1;
-    return 0;
-}
-
 static uint32_t orc_pair_key(uint64_t seed, uint64_t l, uint32_t step)
 {
     uint32_t w[4];
@@ -141,24 +131,49 @@ static uint32_t orc_pair_key(uint64_t seed, uint64_t l, uint32_t step)
     return w[0];
 }
 
-/* order[cell_start[j] .. cell_start[j+1]) = cell j's particles in pairing order. */
+/* Random-stream id of particle l: ids[l] when the caller keeps a subset of a
+ * larger particle set (ids = the particles' indices in that set), else l. */
+static uint64_t orc_id(const uint32_t *ids, uint64_t l) { return ids ? (uint64_t)ids[l] : l; }
+
+/* order[cell_start[j] .. cell_start[j+1]) = cell j's particles (storage
+ * indices) in pairing order; keys and ties use the particles' ids. */
+int orc_pair_order_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t *ids, uint64_t seed,
+                       uint32_t step, uint64_t *cell_start, uint32_t *order);
+
 int orc_pair_order(int64_t n, int32_t M, const int32_t *cell, uint64_t seed, uint32_t step,
                    uint64_t *cell_start, uint32_t *order)
+{
+    return orc_pair_order_ids(n, M, cell, NULL, seed, step, cell_start, order);
+}
+
+typedef struct { uint32_t key; uint32_t id; uint32_t l; } orc_kil;
+
+static int orc_kil_cmp(const void *a, const void *b)
+{
+    const orc_kil *x = (const orc_kil *)a, *y = (const orc_kil *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->id != y->id) return x->id < y->id ? -1 : 1;
+    return 0;
+}
+
+int orc_pair_order_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t *ids, uint64_t seed,
+                       uint32_t step, uint64_t *cell_start, uint32_t *order)
 {
     uint32_t *counts = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)M);
     if (!counts) return ORC_EINVAL;
     int rc = orc_group(n, M, cell, counts, cell_start, order);
     free(counts);
     if (rc) return rc;
-    orc_kl *tmp = (orc_kl *)malloc(sizeof(orc_kl) * (size_t)(n > 0 ? n : 1));
+    orc_kil *tmp = (orc_kil *)malloc(sizeof(orc_kil) * (size_t)(n > 0 ? n : 1));
     if (!tmp) return ORC_EINVAL;
     for (int32_t j = 0; j < M; ++j) {
         uint64_t s = cell_start[j], e = cell_start[j + 1];
         for (uint64_t k = s; k < e; ++k) {
             tmp[k - s].l = order[k];
-            tmp[k - s].key = orc_pair_key(seed, order[k], step);
+            tmp[k - s].id = (uint32_t)orc_id(ids, order[k]);
+            tmp[k - s].key = orc_pair_key(seed, orc_id(ids, order[k]), step);
         }
-        qsort(tmp, (size_t)(e - s), sizeof(orc_kl), orc_kl_cmp);
+        qsort(tmp, (size_t)(e - s), sizeof(orc_kil), orc_kil_cmp);
         for (uint64_t k = s; k < e; ++k) order[k] = tmp[k - s].l;
     }
     free(tmp);
@@ -258,15 +273,26 @@ static void orc_cell_mean_k(const uint32_t *idx, uint64_t cnt, const double *vx,
     *K = s;
 }
 
+int orc_coulomb_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t *ids, double *vx, double *vy,
+                    double *vz, const double *inv_vol, const double *lnlam, const double *dt,
+                    const orc_params *p, uint32_t step);
+
 int orc_coulomb(int64_t n, int32_t M, const int32_t *cell, double *vx, double *vy, double *vz,
                 const double *inv_vol, const double *lnlam, const double *dt,
                 const orc_params *p, uint32_t step)
+{
+    return orc_coulomb_ids(n, M, cell, NULL, vx, vy, vz, inv_vol, lnlam, dt, p, step);
+}
+
+int orc_coulomb_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t *ids, double *vx, double *vy,
+                    double *vz, const double *inv_vol, const double *lnlam, const double *dt,
+                    const orc_params *p, uint32_t step)
 {
     if (n < 0 || M <= 0) return ORC_EINVAL;
     uint64_t *cs = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1));
     uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     if (!cs || !order) { free(cs); free(order); return ORC_EINVAL; }
-    int rc = orc_pair_order(n, M, cell, p->seed, step, cs, order);
+    int rc = orc_pair_order_ids(n, M, cell, ids, p->seed, step, cs, order);
     if (rc) { free(cs); free(order); return rc; }
     for (int32_t j = 0; j < M; ++j) {
         uint64_t s = cs[j], cnt = cs[j + 1] - cs[j];
@@ -277,8 +303,9 @@ int orc_coulomb(int64_t n, int32_t M, const int32_t *cell, double *vx, double *v
         double A = orc_ta_coefficient(p, p->weight * (double)cnt * inv_vol[j], lnlam[j], dt[j]);
         for (uint64_t k = 0; k + 1 < cnt; k += 2) {            /* CCS4 + CCS5 per pair */
             uint32_t a = o[k], b = o[k + 1];
+            uint64_t ia = orc_id(ids, a), ib = orc_id(ids, b);
             uint32_t w[4];
-            orc_draw(p->seed, a < b ? a : b, step, ORC_TAG_PAIR, w);
+            orc_draw(p->seed, ia < ib ? ia : ib, step, ORC_TAG_PAIR, w);
             double va[3] = {vx[a], vy[a], vz[a]}, vb[3] = {vx[b], vy[b], vz[b]};
             orc_ta_pair(va, vb, A, w);
             vx[a] = va[0]; vy[a] = va[1]; vz[a] = va[2];
@@ -329,10 +356,23 @@ static void orc_iso_dir(uint32_t wa, uint32_t wb, double d[3])
     d[0] = s * cos(ph); d[1] = s * sin(ph); d[2] = c;
 }
 
+int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, const uint32_t *ids, double *x,
+                    double *vx, double *vy, double *vz, const double *dt, const orc_params *p,
+                    uint32_t step, int64_t *counts_out, int8_t *decision, double *margin);
+
 int orc_neutral(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, double *x,
                 double *vx, double *vy, double *vz, const double *dt, const orc_params *p,
                 uint32_t step, int64_t *counts_out /* [3]: candidates, elastic, ionization */,
                 int8_t *decision, double *margin)
+{
+    return orc_neutral_ids(n_io, capacity, M, cell, NULL, x, vx, vy, vz, dt, p, step, counts_out, decision, margin);
+}
+
+/* With `ids`, random streams use ids[l]; appended secondaries get no id here
+ * (ids[n..] is left to the caller). */
+int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, const uint32_t *ids, double *x,
+                    double *vx, double *vy, double *vz, const double *dt, const orc_params *p,
+                    uint32_t step, int64_t *counts_out, int8_t *decision, double *margin)
 {
     int64_t n = *n_io;
     if (n < 0 || M <= 0) return ORC_EINVAL;
@@ -353,7 +393,7 @@ int orc_neutral(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, doubl
         double numax = p->n_neutral * sig_tot * sqrt(vmax2[j]);
         double pnull = -expm1(-numax * dt[j]);
         uint32_t w[4];
-        orc_draw(p->seed, (uint64_t)l, step, ORC_TAG_PARTICLE, w);
+        orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_PARTICLE, w);
         double uc = orc_uniform(w[1]);
         if (decision) decision[l] = 0;
         if (margin) margin[l] = fabs(uc - pnull);
@@ -378,7 +418,7 @@ int orc_neutral(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, doubl
         }
         if (kind == 1) continue;
         uint32_t s[4];
-        orc_draw(p->seed, (uint64_t)l, step, ORC_TAG_SCATTER, s);
+        orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_SCATTER, s);
         double d[3];
         orc_iso_dir(s[0], s[1], d);
         if (kind == 2) {
@@ -394,7 +434,7 @@ int orc_neutral(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, doubl
             double Eprim = Ep - Es;
             double vp = sqrt(2.0 * Eprim * e_over_m), vs = sqrt(2.0 * Es * e_over_m);
             uint32_t t[4];
-            orc_draw(p->seed, (uint64_t)l, step, ORC_TAG_SECONDARY, t);
+            orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_SECONDARY, t);
             double ds[3];
             orc_iso_dir(t[0], t[1], ds);
             vx[l] = vp * d[0]; vy[l] = vp * d[1]; vz[l] = vp * d[2];
@@ -410,7 +450,7 @@ int orc_neutral(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, doubl
         /* cells in ascending order; inside a cell, parents in pairing order */
         uint64_t *cs = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1));
         uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-        if (!cs || !order || orc_pair_order(n, M, cell, p->seed, step, cs, order) != ORC_OK) {
+        if (!cs || !order || orc_pair_order_ids(n, M, cell, ids, p->seed, step, cs, order) != ORC_OK) {
             rc = ORC_EINVAL;
         } else {
             int64_t dst = n;

@@ -227,6 +227,7 @@ def subset_cells(wl: dict, cells) -> dict:
     remap[cells] = np.arange(cells.size)
     keep = remap[wl["cell"]] >= 0
     out = dict(wl)
+    out["ids"] = np.nonzero(keep)[0].astype(np.uint32)    # original indices: the random-stream ids
     out.update(M=int(cells.size), vx=wl["vx"][keep], vy=wl["vy"][keep], vz=wl["vz"][keep],
                cell=remap[wl["cell"][keep]].astype(np.int32), inv_vol=wl["inv_vol"][cells],
                dt_cell=wl["dt_cell"][cells], lnlam_cell=wl["lnlam_cell"][cells])
