@@ -1,0 +1,109 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch configuration
+bench.py times (default class table, CUDA graph): one step on the GPU over the
+whole workload, then the FP64 oracle on a sample of cells (with the particles'
+original ids) -- the smallest and largest cells and a random selection.
+FP32 per-cell moments must agree within 1e-5 (cells with a null-collision
+decision inside the oracle's 1e-6 margin excepted and counted)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_06771_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_06771_gb300 import build as B
+    from paper_2508_06771_gb300 import ltpc
+    B.build()
+    ltpc.load_library()
+    return ltpc
+
+
+def _moment_errors(mom, omom):
+    N = np.maximum(omom[:, 0], 1)
+    vth = np.sqrt(omom[:, 5:8].sum(1) / N)
+    e = np.zeros_like(omom)
+    e[:, 0] = np.abs(mom[:, 0] - omom[:, 0])
+    e[:, 2:5] = np.abs(mom[:, 2:5] - omom[:, 2:5]) / (N * vth)[:, None]
+    for k in (5, 6, 7, 8, 9):
+        e[:, k] = np.abs(mom[:, k] - omom[:, k]) / np.maximum(np.abs(omom[:, k]), 1e-300)
+    z = omom[:, 9] == 0
+    e[z, 9] = (np.abs(mom[z, 9]) > 0).astype(float)
+    return e
+
+
+def _sample_cells(counts, k, seed):
+    order = np.argsort(counts, kind="stable")
+    rng = np.random.default_rng(seed)
+    pick = set(order[:4].tolist()) | set(order[-4:].tolist())
+    pick |= set(rng.choice(counts.size, size=min(k, counts.size), replace=False).tolist())
+    return np.array(sorted(pick))
+
+
+def _check(L, orc, wl, cells, neutral, step=0):
+    col = L.Collider.from_workload(wl)
+    col.load_workload(wl)
+    col.step(wl["dt"] if "dt" in wl else col.dt, step)
+    mom, _ = col.moments()
+    col.sync()
+    col.close()
+    sub = W.subset_cells(wl, cells)
+    for k in ("vx", "vy", "vz"):
+        sub[k] = np.asarray(sub[k], np.float32).astype(np.float64)
+    P = orc.make_params(sub, correction=True)
+    st = orc.State(sub)
+    lnlam = None
+    if sub.get("lnlam_mode", 0) == 1:
+        m0, _ = orc.moments(st, P)
+        lnlam = orc.lnlambda_from_moments(m0, sub["inv_vol"], sub["weight"], sub["mass"], sub["charge"])
+    orc.coulomb(st, P, step, lnlam)
+    near = np.zeros(sub["M"], bool)
+    if neutral:
+        probe = orc.State(sub)
+        probe.vx[:], probe.vy[:], probe.vz[:] = st.vx, st.vy, st.vz
+        dec = orc.neutral(probe, P, step, with_decisions=True)
+        near[st.cell[:st.n][dec["margin"] < 1e-6]] = True
+        orc.neutral(st, P, step)
+    omom, _ = orc.moments(st, P)
+    e = _moment_errors(mom[cells], omom)
+    ok = ~near
+    assert near.sum() <= max(2, cells.size // 50), near.sum()
+    assert e[ok, 0].max() == 0
+    worst = e[ok][:, 2:9].max(axis=0)
+    assert worst.max() <= FP32_TOL, worst
+    return worst
+
+
+def test_cfg2_full_size_sampled(L, orc):
+    wl = W.cfg2()                                      # 4096 cells x 10000, FP32, Coulomb + e-n
+    for k in ("vx", "vy", "vz"):
+        wl[k] = wl[k].astype(np.float32)
+    cells = _sample_cells(np.full(wl["M"], 10000), 48, 1)
+    _check(L, orc, wl, cells, neutral=True)
+
+
+def test_cfg3_full_size_sampled(L, orc):
+    wl = W.cfg3(dtype=np.float32)                      # 256x256 cells, 16..65536 per cell, NRL lnL
+    cells = _sample_cells(wl["counts"], 120, 2)
+    _check(L, orc, wl, cells, neutral=False)
+
+
+def test_cfg4_full_size_sampled(L, orc):
+    wl = W.cfg4(dtype=np.float32)                      # 64 instances, ~1.19e9 particles
+    inst = wl["instance_of_cell"]
+    counts = np.bincount(wl["cell"], minlength=wl["M"])
+    rng = np.random.default_rng(3)
+    cells = []
+    for i in np.unique(inst):                           # two cells of every instance
+        cs = np.nonzero(inst == i)[0]
+        cells += rng.choice(cs, size=min(2, cs.size), replace=False).tolist()
+    cells = np.array(sorted(set(cells) | set(_sample_cells(counts, 0, 4).tolist())))
+    _check(L, orc, wl, cells, neutral=False)
