@@ -46,13 +46,24 @@ struct Cl {
 };
 
 // Elementary functions per working precision.  binary32 uses the SFU
-// approximations (relative errors ~1e-7, far inside the 1e-5 moment bar);
-// binary64 uses correctly rounded or library functions (1e-12 velocity bar).
+// approximations, one MUFU instruction each (relative errors ~1e-7, far inside
+// the 1e-5 moment bar); binary64 uses correctly rounded or library functions
+// (1e-12 velocity bar).
 template <class T> struct Math;
 template <> struct Math<float> {
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
-    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rcp(float x)
+    {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    static __device__ __forceinline__ float sqrt(float x)
+    {
+        float y;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
     static __device__ __forceinline__ float ln(float x) { return __logf(x); }
     // sin and cos of 2 pi u for u in (0, 1], evaluated on (-pi, pi]
     static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c)
@@ -68,7 +79,9 @@ template <> struct Math<float> {
         const float t = fmaf(__log2f(E), 0.30102999566398120f * 12.8f, 25.6f);   // (log10 E + 2) 64/5
         if (!(t >= 0.f)) return 0;
         if (t >= 63.f) return 63;
-        return (int)t;
+        // floor(t) for 0 <= t < 2^23 without a float-to-integer conversion: t + 2^23
+        // rounded down has floor(t) as its low mantissa bits
+        return (int)(__float_as_uint(__fadd_rd(t, 8388608.0f)) & 0x7FFFFFu);
     }
 };
 template <> struct Math<double> {
@@ -140,6 +153,16 @@ __device__ __forceinline__ void iso_dir(uint32_t wa, uint32_t wb, T& dx, T& dy, 
     Math<T>::sincos2pi(unif<T>(wb), &sp, &cp);
     dx = s * cp; dy = s * sp; dz = c;
 }
+
+template <class T> struct Vec2;
+template <> struct Vec2<float> {
+    using type = float2;
+    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Vec2<double> {
+    using type = double2;
+    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
 
 template <int NT>
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_scan, uint32_t* total)
@@ -259,6 +282,36 @@ __device__ __forceinline__ A cluster_max(A v, A* s_red, double* s_cl)
 
 __device__ __forceinline__ void flag_error(DevState* ds, uint32_t bit) { atomicOr(&ds->err, bit); }
 
+// Asynchronous global -> shared copy of B bytes (4, 8 or 16; both addresses
+// B-aligned).  Completion: cp_async_wait_all() by the issuing thread, then a
+// barrier before other threads read the destination.
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc)
+{
+    static_assert(B == 4 || B == 8 || B == 16, "cp.async size");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The null-collision candidate test U < P_null decided from the top 16 bits h
+// of the candidate word: the smallest uniform over all words with those bits
+// is below P_null exactly when h < H, with H computed here once per cell
+// (exact: every quantity is a scaled binary32/binary64 value).
+template <class T> __device__ __forceinline__ uint32_t cand_threshold(T pnull);
+template <> __device__ __forceinline__ uint32_t cand_threshold<float>(float pnull)
+{
+    // lo(h) = (256 h + 1) 2^-24 < p  <=>  h < (p 2^24 - 1) / 256
+    const double h = ceil(((double)pnull * 16777216.0 - 1.0) / 256.0);
+    return h <= 0.0 ? 0u : h >= 65536.0 ? 65536u : (uint32_t)h;
+}
+template <> __device__ __forceinline__ uint32_t cand_threshold<double>(double pnull)
+{
+    // lo(h) = (65536 h + 1/2) 2^-32 < p  <=>  h < (p 2^32 - 1/2) / 65536
+    const double h = ceil((pnull * 4294967296.0 - 0.5) / 65536.0);
+    return h <= 0.0 ? 0u : h >= 65536.0 ? 65536u : (uint32_t)h;
+}
+
 // Begins of the C ranges of a split (ltpc_index.h), kept in registers so that
 // the owner of an item is found by C-1 compares instead of a division.
 template <int C>
@@ -293,7 +346,7 @@ struct Bounds {
 template <class T>
 __host__ __device__ constexpr size_t cells_dyn_smem(uint32_t capl)
 {
-    const size_t pair_b = (size_t)capl * (3 * sizeof(T) + 4 + 2);
+    const size_t pair_b = (size_t)capl * (3 * sizeof(T) + 4 + 2) + 16;
     const size_t sort_b = (size_t)capl * 12 + ((size_t)capl + 2) * 4;
     const size_t m = pair_b > sort_b ? pair_b : sort_b;
     return (m + 15) & ~(size_t)15;
@@ -331,7 +384,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     T* svy = svx + CAPL;
     T* svz = svy + CAPL;
     uint32_t* sl = reinterpret_cast<uint32_t*>(svz + CAPL);
-    uint16_t* sw = reinterpret_cast<uint16_t*>(sl + CAPL);
+    // candidate words: by home index during the sort, by position afterwards;
+    // 16 bytes past the sort view's bucket counters, so the sort never overlaps it
+    uint16_t* sw = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(sl + CAPL) + 16);
     // sort-phase view (aliases the pair-phase arrays)
     uint32_t* stg = reinterpret_cast<uint32_t*>(smem);
     uint32_t* ekey = stg + CAPL;
@@ -349,6 +404,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     __shared__ uint32_t s_list[LISTCAP];
     __shared__ uint32_t s_misc[4];
     __shared__ T s_par[16];
+    __shared__ uint4 s_item[2];                     // current / next work item {j, N_j, I_j, valid}
+    __shared__ __align__(16) double s_cp[12];       // cell parameters: dt_factor, lnlam, inv_vol, -, mom[0..7]
 
     const unsigned r = Cl<C>::rank();
     const unsigned tid = threadIdx.x;
@@ -361,25 +418,41 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     const bool do_neut = (a.flags & F_NEUTRAL) != 0u;
     const bool do_corr = (a.flags & F_CORRECTION) != 0u;
 
+    // Work items are taken one ahead: while a cell is processed, the next
+    // ticket is drawn and its item copied into s_item asynchronously.
+    if (r == 0 && tid == 0) {
+        const uint32_t w = atomicAdd(&ds->ticket[a.cls], 1u);
+        const uint4 it = w < list_n ? a.list[w] : make_uint4(0u, 0u, 0u, 0u);
+        for (unsigned q = 0; q < (unsigned)C; ++q) *Cl<C>::at(&s_item[0], q) = it;
+    }
     Cl<C>::sync();   // every CTA of the cluster is running before any remote access
     PhaseClock pc{a.phase_clk, 0};
     pc.start();
 
-    for (;;) {
-        if (r == 0 && tid == 0) {
-            const uint32_t w = atomicAdd(&ds->ticket[a.cls], 1u);
-            for (unsigned q = 0; q < (unsigned)C; ++q) *Cl<C>::at(&s_misc[0], q) = w;
-        }
-        Cl<C>::sync();
-        const uint32_t witem = s_misc[0];
-        if (witem >= list_n) break;
-        const uint32_t j = a.list[witem];
-        const uint32_t n = a.counts[j];
-        const uint32_t s = a.cell_start[j];
+    for (uint32_t par = 0u;; par ^= 1u) {
+        const uint4 item = s_item[par];
+        if (item.w == 0u) break;
+        const uint32_t j = item.x;
+        const uint32_t n = item.y;
+        const uint32_t s = item.z;
+        uint32_t wnext = 0u;
+        if (r == 0 && tid == 0) wnext = atomicAdd(&ds->ticket[a.cls], 1u);
         if (n == 0u || n > (uint32_t)C * CAPL) {          // uniform over the cluster
-            if (n != 0u && r == 0 && tid == 0) flag_error(ds, ERR_CELL_TOO_LARGE);
+            if (r == 0 && tid == 0) {
+                if (n != 0u) flag_error(ds, ERR_CELL_TOO_LARGE);
+                const uint4 it = wnext < list_n ? a.list[wnext] : make_uint4(0u, 0u, 0u, 0u);
+                for (unsigned q = 0; q < (unsigned)C; ++q) *Cl<C>::at(&s_item[par ^ 1u], q) = it;
+            }
             Cl<C>::sync();
             continue;
+        }
+        if (tid == 0) {   // this cell's parameters, consumed after the gather's wait
+            cp_async<8>(&s_cp[0], a.dt_factor + j);
+            cp_async<8>(&s_cp[1], a.lnlam + j);
+            cp_async<8>(&s_cp[2], a.inv_vol + j);
+            const double* m = a.mom + (size_t)j * NMOM;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cp_async<16>(&s_cp[4 + 2 * q], m + 2 * q);
         }
         const uint32_t nb = n_buckets(n);
         const uint32_t hb = split_begin(r, n, C), nh = split_begin(r + 1, n, C) - hb;
@@ -397,23 +470,31 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
 
         pc.mark(0);
         // ---- 1b. home slice: particle ids (coalesced), pairing keys, bucket counts
-        uint32_t hl[ITEMS], hp[ITEMS], hw[ITEMS];
+        uint32_t hl[ITEMS], hp[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {   // all id loads in flight before their first use
+            const uint32_t k = tid + (uint32_t)i * NT;
+            hl[i] = k < nh ? __ldcs(a.perm + s + hb + k) : 0u;
+        }
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
-            hl[i] = 0u; hp[i] = 0u; hw[i] = 0u;
+            hp[i] = 0u;
             if (k < nh) {
-                const uint32_t l = a.perm[s + hb + k];
+                const uint32_t l = hl[i];
                 const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
                 const uint32_t b = __umulhi(rw.x, nb);
                 uint32_t b0;
                 const uint32_t ro = BB.locate(b, b0);
                 const uint32_t slot = atomicAdd(Cl<C>::at(bcnt + (b - b0), ro), 1u);
                 stg[k] = rw.x;
-                hl[i] = l;
+                sw[k] = (uint16_t)(rw.y >> 16);
                 hp[i] = (b << 16) | (slot & 0xFFFFu);
-                hw[i] = rw.y >> 16;
             }
+        }
+        if (r == 0 && tid == 0) {   // the next work item, completed by the wait before phase 3
+            if (wnext < list_n) cp_async<16>(&s_item[par ^ 1u], a.list + wnext);
+            else s_item[par ^ 1u] = make_uint4(0u, 0u, 0u, 0u);
         }
         Cl<C>::sync();
 
@@ -488,38 +569,57 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                         uint32_t t0;
                         const uint32_t o = PB.locate(t, t0);
                         const uint32_t kk = *Cl<C>::at(ekey + (t - t0), o);
-                        const uint32_t ll = *Cl<C>::at(el + (t - t0), o);
-                        rank += (kk < key) || (kk == key && ll < l);
+                        if (kk == key) rank += *Cl<C>::at(el + (t - t0), o) < l ? 1u : 0u;
+                        else rank += kk < key ? 1u : 0u;
                     }
                 } else {
                     flag_error(ds, ERR_INDEX);
                 }
                 uint32_t pos = bs + rank;
                 if (pos >= n) { flag_error(ds, ERR_INDEX); pos = 0u; }
-                hp[i] = pos | (hw[i] << 16);
+                hp[i] = pos | ((uint32_t)sw[k] << 16);
             }
         }
         Cl<C>::sync();
 
         pc.mark(4);
         pc.mark(5);
-        // ---- 2. gather velocities (coalesced through the id list) into pairing order
+        // ---- 2. gather velocities (coalesced through the id list) into pairing order;
+        // single-CTA classes copy them asynchronously, all in flight at once
+        if constexpr (C == 1) {
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t k = tid + (uint32_t)i * NT;
-            if (k < nh) {
-                const uint32_t pos = hp[i] & 0xFFFFu, l = hl[i];
-                uint32_t p0;
-                const uint32_t o = PB.locate(pos, p0);
-                const uint32_t lp = pos - p0;
-                const T x = a.vx[l], y = a.vy[l], z = a.vz[l];
-                *Cl<C>::at(svx + lp, o) = x;
-                *Cl<C>::at(svy + lp, o) = y;
-                *Cl<C>::at(svz + lp, o) = z;
-                *Cl<C>::at(sl + lp, o) = l;
-                *Cl<C>::at(sw + lp, o) = (uint16_t)(hp[i] >> 16);
-                if (a.order_out) a.order_out[s + pos] = l;
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t k = tid + (uint32_t)i * NT;
+                if (k < nh) {
+                    const uint32_t pos = hp[i] & 0xFFFFu, l = hl[i];
+                    cp_async<sizeof(T)>(svx + pos, a.vx + l);
+                    cp_async<sizeof(T)>(svy + pos, a.vy + l);
+                    cp_async<sizeof(T)>(svz + pos, a.vz + l);
+                    sl[pos] = l;
+                    sw[pos] = (uint16_t)(hp[i] >> 16);
+                    if (a.order_out) a.order_out[s + pos] = l;
+                }
             }
+            cp_async_wait_all();
+        } else {
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t k = tid + (uint32_t)i * NT;
+                if (k < nh) {
+                    const uint32_t pos = hp[i] & 0xFFFFu, l = hl[i];
+                    uint32_t p0;
+                    const uint32_t o = PB.locate(pos, p0);
+                    const uint32_t lp = pos - p0;
+                    const T x = a.vx[l], y = a.vy[l], z = a.vz[l];
+                    *Cl<C>::at(svx + lp, o) = x;
+                    *Cl<C>::at(svy + lp, o) = y;
+                    *Cl<C>::at(svz + lp, o) = z;
+                    *Cl<C>::at(sl + lp, o) = l;
+                    *Cl<C>::at(sw + lp, o) = (uint16_t)(hp[i] >> 16);
+                    if (a.order_out) a.order_out[s + pos] = l;
+                }
+            }
+            if (tid == 0) cp_async_wait_all();
         }
         Cl<C>::sync();
 
@@ -530,17 +630,17 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         T vmax2 = T(0);
         if (do_coul && n >= 2u) {
             if (tid == 0) {   // per-cell scalars in double, once per CTA
-                const double dtj = dt * a.dt_factor[j];
-                double lnl = a.lnlam[j];
+                const double dtj = dt * s_cp[0];
+                double lnl = s_cp[1];
                 if (a.flags & F_LNL_NRL) {
-                    const double* m = a.mom + (size_t)j * NMOM;
+                    const double* m = s_cp + 4;
                     const double N = m[0];
                     lnl = 2.0;
                     if (N >= 2.0) {
                         const double mx = m[2] / N, my = m[3] / N, mz = m[4] / N;
                         const double msq = (m[5] + m[6] + m[7]) / N;
                         const double TeV = (msq - (mx * mx + my * my + mz * mz)) / (3.0 * a.e_over_m);
-                        const double nm3 = a.weight * (double)n * a.inv_vol[j];
+                        const double nm3 = a.weight * (double)n * s_cp[2];
                         if (TeV > 0.0 && nm3 > 0.0) {
                             const double lt = log(TeV);
                             const double v = 23.5 - log(sqrt(nm3 * 1e-6) * pow(TeV, -1.25)) -
@@ -549,12 +649,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                         }
                     }
                 }
-                s_par[0] = (T)(a.coef0 * (double)n * a.inv_vol[j] * lnl * dtj);
+                s_par[0] = (T)(a.coef0 * (double)n * s_cp[2] * lnl * dtj);
                 // centring shift for the restoration sums: the cell's mean velocity
                 // at the end of the previous pass (no CTA modifies it in this pass)
                 s_par[1] = s_par[2] = s_par[3] = T(0);
                 if (do_corr) {
-                    const double* m = a.mom + (size_t)j * NMOM;
+                    const double* m = s_cp + 4;
                     if (m[0] > 0.0) {
                         s_par[1] = (T)(m[2] / m[0]); s_par[2] = (T)(m[3] / m[0]); s_par[3] = (T)(m[4] / m[0]);
                     }
@@ -570,18 +670,23 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 acc[o] += dx; acc[o + 1] += dy; acc[o + 2] += dz; acc[o + 3] += dx * dx + dy * dy + dz * dz;
             };
             const uint32_t nslot = (nloc + 1u) / 2u;
+            using V2 = typename Vec2<T>::type;
             for (uint32_t p = tid; p < nslot; p += NT) {
-                const uint32_t ia = 2u * p, ib = ia + 1u;
-                T ax = svx[ia], ay = svy[ia], az = svz[ia];
+                const uint32_t ia = 2u * p, ib = ia + 1u;   // pair slots are even-aligned: one vector access each
+                const V2 X = *reinterpret_cast<const V2*>(svx + ia);
+                const V2 Y = *reinterpret_cast<const V2*>(svy + ia);
+                const V2 Z = *reinterpret_cast<const V2*>(svz + ia);
+                T ax = X.x, ay = Y.x, az = Z.x;
                 if (do_corr) presum(ax, ay, az, 0);
                 if (ib < nloc) {
-                    T bx = svx[ib], by = svy[ib], bz = svz[ib];
-                    const uint32_t la = sl[ia], lb = sl[ib];
+                    T bx = X.y, by = Y.y, bz = Z.y;
+                    const uint2 L2 = *reinterpret_cast<const uint2*>(sl + ia);
                     if (do_corr) presum(bx, by, bz, 0);
-                    const uint4 w = draw(k0, k1, la < lb ? la : lb, step, TAG_PAIR);
+                    const uint4 w = draw(k0, k1, L2.x < L2.y ? L2.x : L2.y, step, TAG_PAIR);
                     ta_collide<T>(ax, ay, az, bx, by, bz, A, w);
-                    svx[ia] = ax; svy[ia] = ay; svz[ia] = az;
-                    svx[ib] = bx; svy[ib] = by; svz[ib] = bz;
+                    *reinterpret_cast<V2*>(svx + ia) = Vec2<T>::make(ax, bx);
+                    *reinterpret_cast<V2*>(svy + ia) = Vec2<T>::make(ay, by);
+                    *reinterpret_cast<V2*>(svz + ia) = Vec2<T>::make(az, bz);
                     if (do_corr) presum(bx, by, bz, 4);
                     else vmax2 = fmax(vmax2, bx * bx + by * by + bz * bz);
                 }
@@ -593,17 +698,18 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 // V = c + S1 / n and K = S2 - |S1|^2 / n, before (0..3) and after (4..7)
                 if (tid < 7u) {   // restoration scalars, one per thread, in the working precision
                     const T inv_n = T(1) / (T)n;
-                    const T S[8] = {(T)s_tot[0], (T)s_tot[1], (T)s_tot[2], (T)s_tot[3],
-                                    (T)s_tot[4], (T)s_tot[5], (T)s_tot[6], (T)s_tot[7]};
                     T val;
                     if (tid == 0) {
-                        const T K0 = S[3] - (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]) * inv_n;
-                        const T K1 = S[7] - (S[4] * S[4] + S[5] * S[5] + S[6] * S[6]) * inv_n;
+                        const T S0 = (T)s_tot[0], S1 = (T)s_tot[1], S2 = (T)s_tot[2], S3 = (T)s_tot[3];
+                        const T S4 = (T)s_tot[4], S5 = (T)s_tot[5], S6 = (T)s_tot[6], S7 = (T)s_tot[7];
+                        const T K0 = S3 - (S0 * S0 + S1 * S1 + S2 * S2) * inv_n;
+                        const T K1 = S7 - (S4 * S4 + S5 * S5 + S6 * S6) * inv_n;
                         val = (K1 > T(0) && K0 > T(0)) ? Math<T>::sqrt(K0 / K1) : T(1);
                     } else {
-                        const int k = (int)tid - 1;            // 0..5 -> V0x V0y V0z V1x V1y V1z
-                        const T c = (k % 3 == 0) ? cx : (k % 3 == 1) ? cy : cz;
-                        val = c + S[(k / 3) * 4 + (k % 3)] * inv_n;
+                        const unsigned k = tid - 1u;            // 0..5 -> V0x V0y V0z V1x V1y V1z
+                        const unsigned comp = k % 3u;
+                        const T c = comp == 0u ? cx : comp == 1u ? cy : cz;
+                        val = c + (T)s_tot[(k / 3u) * 4u + comp] * inv_n;
                     }
                     s_par[4 + tid] = val;
                 }
@@ -637,21 +743,19 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl);
             if (tid == 0) {   // null-collision bound of the cell, in the working precision
                 const T nmx = (T)(a.n_neutral * (a.sigma_el + a.sigma_ion)) * Math<T>::sqrt(md);
+                const T pn = -expm1(-nmx * (T)(dt * s_cp[0]));
                 s_par[11] = nmx;
-                s_par[12] = -expm1(-nmx * (T)(dt * a.dt_factor[j]));
+                s_par[12] = pn;
+                s_misc[0] = cand_threshold<T>(pn);
             }
             for (uint32_t w = tid; w < nw; w += NT) s_imask[w] = 0u;
             __syncthreads();
             const T numax = s_par[11];
             const T pnull = s_par[12];
+            const uint32_t hmin = s_misc[0];
             for (uint32_t q0 = 0; q0 < nloc; q0 += NT) {
                 const uint32_t q = q0 + tid;
-                bool maybe = false;
-                if (q < nloc) {
-                    T lo, up;
-                    unif_hi16_range<T>((uint32_t)sw[q], lo, up);
-                    maybe = lo < pnull;
-                }
+                const bool maybe = q < nloc && (uint32_t)sw[q] < hmin;
                 const unsigned m = __ballot_sync(0xFFFFFFFFu, maybe);
                 if ((tid & 31u) == 0u && q0 + tid < nloc + 31u) s_cmask[(q0 + tid) >> 5] = m;
             }
@@ -692,10 +796,11 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 if (q < r) ion_base += t;
                 all += t;
             }
-            if (r == 0 && tid == 0) a.ion_count[j] = all;
+            if (r == 0 && tid == 0) { a.ion_count[j] = all; s_misc[3] = all; }
             Cl<C>::sync();
         } else if (r == 0 && tid == 0) {
             a.ion_count[j] = 0u;
+            s_misc[3] = 0u;
         }
 
         pc.mark(8);
@@ -753,7 +858,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             }
             if (r == 0 && tid == 0) {
                 double* m = a.mom + (size_t)j * NMOM;
-                const double N = (double)(n + (do_neut ? a.ion_count[j] : 0u));
+                const double N = (double)(n + s_misc[3]);
                 m[0] = N;
                 m[1] = a.weight * N;
                 m[2] = s_tot[0]; m[3] = s_tot[1]; m[4] = s_tot[2];
@@ -776,6 +881,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 a.vx[l] = *Cl<C>::at(svx + lp, o);
                 a.vy[l] = *Cl<C>::at(svy + lp, o);
                 a.vz[l] = *Cl<C>::at(svz + lp, o);
+            }
+        }
+        if constexpr (C > 1) {
+            if (r == 0 && tid == 0) {
+                const uint4 it = s_item[par ^ 1u];
+                for (unsigned q = 1; q < (unsigned)C; ++q) *Cl<C>::at(&s_item[par ^ 1u], q) = it;
             }
         }
         Cl<C>::sync();

@@ -79,7 +79,8 @@ static __global__ void k_scatter(const int32_t* __restrict__ cell, uint32_t* __r
 //   1. if `append`: exclusive scan of this pass's secondaries per cell into
 //      ion_off, capacity check, counts += ion_count, keep the old offsets;
 //   2. CCS2: cell_start = exclusive scan of counts, cursor = cell_start;
-//   3. cluster-class work lists (cells in ascending index order per class);
+//   3. cluster-class work lists (cells in ascending index order per class,
+//      each item {cell, N_j, I_j, 1} so that a CTA fetches it with one load);
 //   4. reset the work tickets, optionally advance the step number.
 static __global__ void __launch_bounds__(REGROUP_THREADS)
 k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_start,
@@ -208,7 +209,7 @@ k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_
             int k = 0;
             while (k < lists.n_classes - 1 && n > lists.max_n[k]) ++k;
             if (n > lists.max_n[k]) atomicOr(&ds->err, ERR_CELL_TOO_LARGE);
-            lists.list[k][pos[k]++] = c;
+            lists.list[k][pos[k]++] = make_uint4(c, n, cell_start[c], 1u);
         }
         if (tid < (unsigned)MAX_CLASSES) {
             ds->class_n[tid] = tid < (unsigned)lists.n_classes ? s_cls[tid][NT / 32] : 0u;

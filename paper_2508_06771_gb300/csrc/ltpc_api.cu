@@ -65,7 +65,7 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->inv_vol = take(M * 8);
     L->dt_factor = take(M * 8);
     L->lnlam = take(M * 8);
-    L->lists = take(M * 4 * MAX_CLASSES);
+    L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
     L->work = o;
     return true;
@@ -128,7 +128,7 @@ int set_table(ltpc_ctx* ctx, int table)
     ctx->lists.n_classes = T.n;
     for (int k = 0; k < MAX_CLASSES; ++k) {
         ctx->lists.max_n[k] = 0;
-        ctx->lists.list[k] = ctx->w<uint32_t>(ctx->L.lists) + (size_t)k * ctx->cfg.n_cells;
+        ctx->lists.list[k] = ctx->w<uint4>(ctx->L.lists) + (size_t)k * ctx->cfg.n_cells;
     }
     for (int k = 0; k < T.n; ++k) {
         const CellKernelEntry& e = ctx->kernels[T.kernel[k]];

@@ -56,7 +56,7 @@ struct CellArgs {
     uint32_t* stage_l;           // parent id of each staged secondary
     T* stage_vx; T* stage_vy; T* stage_vz;
     DevState* ds;
-    const uint32_t* list;        // cells of this class
+    const uint4* list;           // work items of this class: {cell j, N_j, I_j, 1}
     uint32_t cls;
     uint32_t flags;
     uint64_t seed;

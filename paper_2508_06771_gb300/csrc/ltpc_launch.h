@@ -13,7 +13,7 @@ constexpr int REGROUP_THREADS = 1024;
 struct RegroupLists {
     int32_t n_classes;
     uint32_t max_n[MAX_CLASSES];   // largest cell of each class
-    uint32_t* list[MAX_CLASSES];   // device work lists (M entries each)
+    uint4* list[MAX_CLASSES];      // device work lists (M entries each): {cell, N_j, I_j, 1}
 };
 
 // One compiled shape of the cell kernel.

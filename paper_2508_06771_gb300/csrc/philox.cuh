@@ -47,9 +47,19 @@ template <> __device__ __forceinline__ double unif<double>(uint32_t w)
 {
     return fma((double)w, 0x1p-32, 0x1p-33);
 }
+// Built from bits, without an integer-to-float conversion:
+// ((w >> 8) + 1) 2^-24 = (w >> 9) 2^-23 + (((w >> 8) & 1) + 1) 2^-24, where the
+// first term is the mantissa of a float in [1, 2) minus 1 and the sum is exact
+// (the result is a multiple of 2^-24 in (0, 1]).
+__device__ __forceinline__ float unif24(uint32_t u24)   // u24 = w >> 8
+{
+    const float hi = __uint_as_float(0x3F800000u | (u24 >> 1)) - 1.0f;
+    const float lo = __uint_as_float(0x33800000u + ((u24 & 1u) << 23));   // 2^-24 or 2^-23
+    return hi + lo;
+}
 template <> __device__ __forceinline__ float unif<float>(uint32_t w)
 {
-    return __uint2float_rn((w >> 8) + 1u) * 0x1p-24f;
+    return unif24(w >> 8);
 }
 
 // Range of unif(w) over all w sharing the top 16 bits `hi` (used to decide
@@ -62,8 +72,8 @@ template <> __device__ __forceinline__ void unif_hi16_range<double>(uint32_t hi,
 }
 template <> __device__ __forceinline__ void unif_hi16_range<float>(uint32_t hi, float& lo, float& up)
 {
-    lo = __uint2float_rn((hi << 8) + 1u) * 0x1p-24f;
-    up = __uint2float_rn((hi << 8) + 256u) * 0x1p-24f;
+    lo = unif24(hi << 8);
+    up = unif24((hi << 8) | 0xFFu);
 }
 
 }  // namespace ltpc
