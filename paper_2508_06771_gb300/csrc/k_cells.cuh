@@ -65,6 +65,7 @@ template <> struct Math<float> {
         return y;
     }
     static __device__ __forceinline__ float ln(float x) { return __logf(x); }
+    static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
     // sin and cos of 2 pi u for u in (0, 1], evaluated on (-pi, pi]
     static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c)
     {
@@ -89,6 +90,7 @@ template <> struct Math<double> {
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
     static __device__ __forceinline__ double ln(double x) { return ::log(x); }
+    static __device__ __forceinline__ double expm1(double x) { return ::expm1(x); }
     static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
     static __device__ __forceinline__ int ebin(double E)
     {
@@ -153,6 +155,19 @@ __device__ __forceinline__ void iso_dir(uint32_t wa, uint32_t wb, T& dx, T& dy, 
     Math<T>::sincos2pi(unif<T>(wb), &sp, &cp);
     dx = s * cp; dy = s * sp; dz = c;
 }
+
+// Non-negative floating-point values ordered through their bit patterns.
+template <class T> struct MaxBits;
+template <> struct MaxBits<float> {
+    using U = unsigned int;
+    static __device__ __forceinline__ U to(float x) { return __float_as_uint(x); }
+    static __device__ __forceinline__ float from(U u) { return __uint_as_float(u); }
+};
+template <> struct MaxBits<double> {
+    using U = unsigned long long;
+    static __device__ __forceinline__ U to(double x) { return (U)__double_as_longlong(x); }
+    static __device__ __forceinline__ double from(U u) { return __longlong_as_double((long long)u); }
+};
 
 template <class T> struct Vec2;
 template <> struct Vec2<float> {
@@ -301,9 +316,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <class T> __device__ __forceinline__ uint32_t cand_threshold(T pnull);
 template <> __device__ __forceinline__ uint32_t cand_threshold<float>(float pnull)
 {
-    // lo(h) = (256 h + 1) 2^-24 < p  <=>  h < (p 2^24 - 1) / 256
-    const double h = ceil(((double)pnull * 16777216.0 - 1.0) / 256.0);
-    return h <= 0.0 ? 0u : h >= 65536.0 ? 65536u : (uint32_t)h;
+    // lo(h) = (256 h + 1) 2^-24 < p  <=>  h < (p 2^24 - 1) / 256, all in binary32:
+    // p 2^24 is exact, so is p 2^24 - 1 below 2^24 (and at 2^24 the rounding still
+    // gives the same ceiling, 65536), so are the scaling by 1/256 and the ceiling
+    const float h = ceilf((pnull * 16777216.0f - 1.0f) * 0.00390625f);
+    if (!(h > 0.0f)) return 0u;
+    if (h >= 65536.0f) return 65536u;
+    return __float_as_uint(h + 8388608.0f) & 0x7FFFFFu;   // integer-valued h < 2^23
 }
 template <> __device__ __forceinline__ uint32_t cand_threshold<double>(double pnull)
 {
@@ -404,7 +423,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     __shared__ uint32_t s_list[LISTCAP];
     __shared__ uint32_t s_misc[4];
     __shared__ T s_par[16];
-    __shared__ uint4 s_item[2];                     // current / next work item {j, N_j, I_j, valid}
+    __shared__ uint4 s_item[2];
+    __shared__ typename MaxBits<T>::U s_vmax;         // largest squared speed (bit pattern)                     // current / next work item {j, N_j, I_j, valid}
     __shared__ __align__(16) double s_cp[12];       // cell parameters: dt_factor, lnlam, inv_vol, -, mom[0..7]
 
     const unsigned r = Cl<C>::rank();
@@ -466,6 +486,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // ---- 1a. zero this CTA's bucket counters and histogram
         for (uint32_t i = tid; i <= nbl; i += NT) bcnt[i] = 0u;
         for (uint32_t i = tid; i < 4u * NBIN; i += NT) s_hist[i] = 0u;
+        for (uint32_t i = tid; i < CAPL / 32u; i += NT) s_imask[i] = 0u;
+        if (tid == 0) s_vmax = 0u;
         Cl<C>::sync();
 
         pc.mark(0);
@@ -740,29 +762,43 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         uint32_t ion_base = 0u;      // secondaries of lower-ranked CTAs of this cell
         const T half_m_over_e = a.c_half_m_over_e;
         if (do_neut) {
-            const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl);
-            if (tid == 0) {   // null-collision bound of the cell, in the working precision
-                const T nmx = (T)(a.n_neutral * (a.sigma_el + a.sigma_ion)) * Math<T>::sqrt(md);
-                const T pn = -expm1(-nmx * (T)(dt * s_cp[0]));
-                s_par[11] = nmx;
-                s_par[12] = pn;
-                s_misc[0] = cand_threshold<T>(pn);
+            T numax, pnull;
+            uint32_t hmin;
+            auto bound = [&](T md, T& nmx, T& pn, uint32_t& h) {   // null-collision bound of the cell
+                nmx = a.c_nsig_tot * Math<T>::sqrt(md);
+                pn = -Math<T>::expm1(-nmx * s_par[13]);
+                h = cand_threshold<T>(pn);
+            };
+            if constexpr (C == 1) {
+                // largest squared speed: warp butterfly, then one shared atomicMax on
+                // the bit pattern (monotone for non-negative values), one barrier
+                T v = vmax2;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+                if ((tid & 31u) == 0u) atomicMax(&s_vmax, MaxBits<T>::to(v));
+                if (tid == 0) s_par[13] = (T)(dt * s_cp[0]);
+                __syncthreads();
+                const T md = MaxBits<T>::from(s_vmax);
+                if constexpr (sizeof(T) == 4) {
+                    bound(md, numax, pnull, hmin);       // every thread, in binary32
+                } else {
+                    if (tid == 0) bound(md, s_par[11], s_par[12], s_misc[0]);
+                    __syncthreads();
+                    numax = s_par[11]; pnull = s_par[12]; hmin = s_misc[0];
+                }
+            } else {
+                const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl);
+                if (tid == 0) {
+                    s_par[13] = (T)(dt * s_cp[0]);
+                    bound(md, s_par[11], s_par[12], s_misc[0]);
+                }
+                __syncthreads();
+                numax = s_par[11]; pnull = s_par[12]; hmin = s_misc[0];
             }
-            for (uint32_t w = tid; w < nw; w += NT) s_imask[w] = 0u;
-            __syncthreads();
-            const T numax = s_par[11];
-            const T pnull = s_par[12];
-            const uint32_t hmin = s_misc[0];
-            for (uint32_t q0 = 0; q0 < nloc; q0 += NT) {
-                const uint32_t q = q0 + tid;
-                const bool maybe = q < nloc && (uint32_t)sw[q] < hmin;
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, maybe);
-                if ((tid & 31u) == 0u && q0 + tid < nloc + 31u) s_cmask[(q0 + tid) >> 5] = m;
-            }
-            __syncthreads();
             const T nsel = a.c_nsig_el, nsion = a.c_nsig_ion;
             const T e_ion = a.c_e_ion, mr2 = a.c_mratio2;
-            for_each_masked<NT>(s_cmask, nw, s_list, s_scan, [&](uint32_t q) {
+            bool ionized = false;
+            auto collide = [&](uint32_t q) {
                 const uint32_t l = sl[q];
                 const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
                 if (!(unif<T>(rw.y) < pnull)) return;
@@ -782,25 +818,51 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     svx[q] = vn * dx; svy[q] = vn * dy; svz[q] = vn * dz;
                 } else if (rr < nu_el + nu_ion) {              // C2: ionization, resolved below
                     atomicOr(&s_imask[q >> 5], 1u << (q & 31u));
+                    ionized = true;
                 }
-            });
-            // ranks of this CTA's ionizations in position order, then across the cluster
-            uint32_t tot;
-            const uint32_t wex = block_excl_scan<NT>(tid < nw ? (uint32_t)__popc(s_imask[tid]) : 0u, s_scan, &tot);
-            if (tid < nw) s_ioff[tid] = wex;
-            if (tid == 0) s_misc[2] = tot;
-            Cl<C>::sync();
-            uint32_t all = 0u;
-            for (unsigned q = 0; q < (unsigned)C; ++q) {
-                const uint32_t t = *Cl<C>::at(&s_misc[2], q);
-                if (q < r) ion_base += t;
-                all += t;
+            };
+            // candidate bit mask over local positions, then block-wide compaction
+            for (uint32_t q0 = 0; q0 < nloc; q0 += NT) {
+                const uint32_t q = q0 + tid;
+                const bool maybe = q < nloc && (uint32_t)sw[q] < hmin;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, maybe);
+                if ((tid & 31u) == 0u && q0 + tid < nloc + 31u) s_cmask[(q0 + tid) >> 5] = m;
             }
-            if (r == 0 && tid == 0) { a.ion_count[j] = all; s_misc[3] = all; }
-            Cl<C>::sync();
-        } else if (r == 0 && tid == 0) {
-            a.ion_count[j] = 0u;
-            s_misc[3] = 0u;
+            __syncthreads();
+            for_each_masked<NT>(s_cmask, nw, s_list, s_scan, collide);
+            // ranks of this CTA's ionizations in position order, then across the cluster
+            if constexpr (C == 1) {
+                if (__syncthreads_or(ionized ? 1 : 0)) {
+                    uint32_t tot;
+                    const uint32_t wex = block_excl_scan<NT>(tid < nw ? (uint32_t)__popc(s_imask[tid]) : 0u, s_scan, &tot);
+                    if (tid < nw) s_ioff[tid] = wex;
+                    if (tid == 0) { s_misc[2] = tot; a.ion_count[j] = tot; s_misc[3] = tot; }
+                } else if (tid == 0) {
+                    s_misc[2] = 0u; a.ion_count[j] = 0u; s_misc[3] = 0u;
+                }
+                __syncthreads();
+            } else {
+                __syncthreads();
+                uint32_t tot;
+                const uint32_t wex = block_excl_scan<NT>(tid < nw ? (uint32_t)__popc(s_imask[tid]) : 0u, s_scan, &tot);
+                if (tid < nw) s_ioff[tid] = wex;
+                if (tid == 0) s_misc[2] = tot;
+                Cl<C>::sync();
+                uint32_t all = 0u;
+                for (unsigned q = 0; q < (unsigned)C; ++q) {
+                    const uint32_t t = *Cl<C>::at(&s_misc[2], q);
+                    if (q < r) ion_base += t;
+                    all += t;
+                }
+                if (r == 0 && tid == 0) { a.ion_count[j] = all; s_misc[3] = all; }
+                Cl<C>::sync();
+            }
+        } else {
+            if (tid == 0) s_misc[2] = 0u;
+            if (r == 0 && tid == 0) {
+                a.ion_count[j] = 0u;
+                s_misc[3] = 0u;
+            }
         }
 
         pc.mark(8);

@@ -178,6 +178,7 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.c_two_e_over_m = (T)(2.0 * ctx->cfg.charge / ctx->cfg.mass);
     a.c_nsig_el = (T)(ctx->cfg.n_neutral * ctx->cfg.sigma_el);
     a.c_nsig_ion = (T)(ctx->cfg.n_neutral * ctx->cfg.sigma_ion);
+    a.c_nsig_tot = (T)(ctx->cfg.n_neutral * (ctx->cfg.sigma_el + ctx->cfg.sigma_ion));
     a.c_e_ion = (T)ctx->cfg.e_ion;
     a.c_mratio2 = (T)a.mratio2;
     a.order_out = nullptr;

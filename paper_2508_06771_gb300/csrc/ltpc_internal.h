@@ -67,6 +67,7 @@ struct CellArgs {
     T c_half_m_over_e;           // m / (2 e): squared speed -> energy in eV
     T c_two_e_over_m;            // 2 e / m: energy in eV -> squared speed
     T c_nsig_el, c_nsig_ion;     // n_n sigma_el, n_n sigma_ion
+    T c_nsig_tot;                // n_n (sigma_el + sigma_ion), rounded once
     T c_e_ion, c_mratio2;
     uint32_t* order_out;         // optional: pairing order written at I_j + position
     unsigned long long* phase_clk; // optional: SM cycles spent per kernel phase (tracing)
