@@ -99,14 +99,23 @@ int ltpc_create(ltpc_ctx** out, const ltpc_config* cfg, void* d_state, void* d_w
  * device buffers.  NULL is ignored. */
 void ltpc_destroy(ltpc_ctx* ctx);
 
+/* Flags of ltpc_load_particles. */
+#define LTPC_LOAD_SRC_DEVICE 1   /* sources are device pointers (else host memory) */
+#define LTPC_LOAD_ASYNC 2        /* do not wait on the stream; report device-detected errors later */
+
 /* Load n particles: cell ids (int32, in [0, M)), optional positions x (only
  * if has_position, else ignored), velocities vx, vy, vz in the context's
- * precision.  src_is_device selects host or device sources.  Builds the
- * per-cell grouping (CCS1-CCS3) and the moments of the loaded state.
- * Synchronizing.  Errors: EINVAL (n < 0 or n > capacity), ENONFINITE,
- * EINVAL for cell ids out of range (reported by this call), ECUDA. */
+ * precision.  flags: LTPC_LOAD_SRC_DEVICE selects device sources (host
+ * sources should be pinned for full copy bandwidth); LTPC_LOAD_ASYNC makes
+ * the call asynchronous.  Builds the per-cell grouping (CCS1-CCS3) and the
+ * moments of the loaded state.
+ * Synchronizing by default.  Errors: EINVAL (n < 0, n > capacity or unknown
+ * flags), ECUDA; ENONFINITE and EINVAL for cell ids out of range are reported
+ * by this call, or with LTPC_LOAD_ASYNC by the next ltpc_sync / ltpc_moments
+ * (particles with bad cell ids are then left out of the grouping; host
+ * sources must stay unchanged until the stream reaches the copy). */
 int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const void* x,
-                        const void* vx, const void* vy, const void* vz, int src_is_device);
+                        const void* vx, const void* vy, const void* vz, int flags);
 
 /* Step S1 only: Takizuka-Abe Coulomb collisions (Sec. 4.4) with time step
  * dt (cell j uses dt * dt_factor[j]) at step number `step` (0 <= step <

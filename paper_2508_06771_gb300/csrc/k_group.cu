@@ -28,11 +28,12 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
     }
 }
 
-// CCS3: perm[I_j + rank] = l.  Each warp takes 128 consecutive particles (4 per
+// CCS3: perm[I_j + rank] = l.  Cell ids outside [0, M) are skipped (the load's
+// histogram reports them).  Each warp takes 128 consecutive particles (4 per
 // lane, 16-byte loads).  When they all belong to one cell -- the usual case for
 // cell-grouped storage -- one cursor atomic serves the 128 and the ids are
 // written with 16-byte stores; otherwise one atomic per warp and cell.
-static __global__ void k_scatter(const int32_t* __restrict__ cell, uint32_t* __restrict__ cursor,
+static __global__ void k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
                                  uint32_t* __restrict__ perm, const DevState* __restrict__ ds)
 {
     const unsigned long long n = ds->n;
@@ -49,6 +50,8 @@ static __global__ void k_scatter(const int32_t* __restrict__ cell, uint32_t* __r
 #pragma unroll
             for (int u = 0; u < 4; ++u) c[u] = l0 + u < n ? cell[l0 + u] : -1;
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = c[u] < M ? c[u] : -1;
         const int32_t c0 = __shfl_sync(0xFFFFFFFFu, c[0], 0);
         const bool same = c[0] == c0 && c[1] == c0 && c[2] == c0 && c[3] == c0;
         if (__all_sync(0xFFFFFFFFu, same) && c0 >= 0) {           // one cell, 128 particles
@@ -280,10 +283,10 @@ cudaError_t launch_hist(const int32_t* cell, uint32_t* counts, int32_t M, DevSta
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const int32_t* cell, uint32_t* cursor, uint32_t* perm, const DevState* ds, int grid,
-                           cudaStream_t s)
+cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uint32_t* perm, const DevState* ds,
+                           int grid, cudaStream_t s)
 {
-    k_scatter<<<grid, 256, 0, s>>>(cell, cursor, perm, ds);
+    k_scatter<<<grid, 256, 0, s>>>(cell, M, cursor, perm, ds);
     return cudaGetLastError();
 }
 

@@ -197,7 +197,7 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
     int ei = 0;
     auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[ei++], s) : cudaSuccess; };
     CK(mark());
-    CK(launch_scatter(ctx->s<int32_t>(L.cell), ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
+    CK(launch_scatter(ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
                       grid_stream, s));
     CK(mark());
     CellArgs<T> a = make_args<T>(ctx, flags);
@@ -394,13 +394,15 @@ void ltpc_destroy(ltpc_ctx* ctx)
 }
 
 int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const void* x, const void* vx,
-                        const void* vy, const void* vz, int src_is_device)
+                        const void* vy, const void* vz, int flags)
 {
     if (!ctx || n < 0 || n > ctx->cfg.capacity) return LTPC_EINVAL;
     if (n > 0 && (!cell || !vx || !vy || !vz)) return LTPC_EINVAL;
+    if (flags & ~(LTPC_LOAD_SRC_DEVICE | LTPC_LOAD_ASYNC)) return LTPC_EINVAL;
+    const bool async = (flags & LTPC_LOAD_ASYNC) != 0;
     const Layout& L = ctx->L;
     cudaStream_t s = ctx->stream;
-    const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kind = (flags & LTPC_LOAD_SRC_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t nb = (size_t)n * ctx->es;
     if (n > 0) {
         CK(cudaMemcpyAsync(ctx->st + L.vx, vx, nb, kind, s));
@@ -420,7 +422,7 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
     else
         CK(launch_check_finite<double>(ctx->s<double>(L.vx), ctx->s<double>(L.vy), ctx->s<double>(L.vz), ctx->ds,
                                        ctx->sms * 4, s));
-    int rc = read_errors(ctx);
+    int rc = async ? LTPC_OK : read_errors(ctx);
     if (rc) return rc;
     CK(launch_regroup(ctx->cfg.n_cells, ctx->w<uint32_t>(L.counts), ctx->w<uint32_t>(L.cell_start),
                       ctx->w<uint32_t>(L.cs_prev), ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.ion_count),
@@ -430,7 +432,7 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
     rc = enqueue(ctx, 0u, false);
     if (rc) return rc;
     ctx->next_step = -1;
-    return read_errors(ctx);
+    return async ? LTPC_OK : read_errors(ctx);
 }
 
 int ltpc_collide_coulomb(ltpc_ctx* ctx, double dt, int64_t step)
@@ -580,7 +582,7 @@ int ltpc_grouping(ltpc_ctx* ctx, uint32_t* d_cell_start, uint32_t* d_perm, uint3
     if (!ctx) return LTPC_EINVAL;
     const size_t M = (size_t)ctx->cfg.n_cells;
     // the grouping of the current particles: redo CCS3 into perm
-    CK(launch_scatter(ctx->s<int32_t>(ctx->L.cell), ctx->w<uint32_t>(ctx->L.cursor), ctx->w<uint32_t>(ctx->L.perm),
+    CK(launch_scatter(ctx->s<int32_t>(ctx->L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(ctx->L.cursor), ctx->w<uint32_t>(ctx->L.perm),
                       ctx->ds, ctx->sms * 8, ctx->stream));
     // restore the cursors for the next pass
     CK(cudaMemcpyAsync(ctx->w<uint32_t>(ctx->L.cursor), ctx->w<uint32_t>(ctx->L.cell_start), M * 4,

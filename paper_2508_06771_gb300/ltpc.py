@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libltpc.so")
 
 OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EINTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
 F32, F64 = 0, 1
+LOAD_SRC_DEVICE, LOAD_ASYNC = 1, 2   # flags of ltpc_load_particles
 LNL_CONST, LNL_NRL = 0, 1
 
 _lock = threading.Lock()
@@ -209,19 +210,23 @@ class Collider:
         vxd, vyd, vzd = (self._dev(v, self.dtype) for v in (vx, vy, vz))
         cd = self._dev(cell, t.int32)
         xd = self._dev(x, self.dtype) if x is not None else None
-        self._check(self.L.ltpc_load_particles(self.ctx, n, _ptr(cd), _ptr(xd), _ptr(vxd), _ptr(vyd), _ptr(vzd), 1),
+        self._check(self.L.ltpc_load_particles(self.ctx, n, _ptr(cd), _ptr(xd), _ptr(vxd), _ptr(vyd), _ptr(vzd),
+                                               LOAD_SRC_DEVICE),
                     "load_particles")
         self._keep = (vxd, vyd, vzd, cd, xd)
         return self
 
-    def load_host(self, vx, vy, vz, cell, x=None):
-        """Load from host arrays (numpy, pinned tensors) through the C ABI's host path."""
+    def load_host(self, vx, vy, vz, cell, x=None, asynchronous=False):
+        """Load from host arrays (numpy views of pinned tensors for full bandwidth) through the
+        C ABI's host path.  With `asynchronous`, the call does not wait on the stream (the arrays
+        must stay alive and unchanged until the stream has copied them; errors surface at `sync`)."""
         arrs = [np.ascontiguousarray(v, dtype=self.np_dtype) for v in (vx, vy, vz)]
         c = np.ascontiguousarray(cell, dtype=np.int32)
         xa = np.ascontiguousarray(x, dtype=self.np_dtype) if x is not None else None
         p = lambda a: a.ctypes.data if a is not None else None
-        self._check(self.L.ltpc_load_particles(self.ctx, c.size, p(c), p(xa), p(arrs[0]), p(arrs[1]), p(arrs[2]), 0),
-                    "load_particles")
+        flags = LOAD_ASYNC if asynchronous else 0
+        self._check(self.L.ltpc_load_particles(self.ctx, c.size, p(c), p(xa), p(arrs[0]), p(arrs[1]), p(arrs[2]),
+                                               flags), "load_particles")
         return self
 
     def load_workload(self, wl):
@@ -358,6 +363,8 @@ class Surrogate:
             raise LtpcError(rc, "mlp_create")
         self.h = h
         self.nparam = int(self.L.ltpc_mlp_param_count())
+        # the library starts with the identity normalisation (mean 0, std 1, target scale 1)
+        self.norm = (np.zeros(self.DIN, np.float32), np.ones(self.DIN, np.float32), np.ones(self.DOUT, np.float32))
         self.loss_buf = torch.zeros(1, dtype=torch.float32, device=self.device)
 
     def _chk(self, rc, where):

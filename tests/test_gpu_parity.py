@@ -269,3 +269,30 @@ def test_bad_cell_and_nonfinite_rejected(L):
     with pytest.raises(L.LtpcError) as ei:
         col.load(vx, wl["vy"], wl["vz"], wl["cell"])
     assert ei.value.code == L.ENONFINITE
+
+
+def test_async_load_matches_sync_and_defers_errors(L):
+    """LTPC_LOAD_ASYNC: the same state as a synchronous load; a bad cell id is
+    reported by the next sync, and the particles with valid ids are stepped."""
+    import torch
+    wl = W.ragged(M=16, mean_ppc=300, seed=6, with_empty=True)
+    host = [torch.from_numpy(np.ascontiguousarray(wl[k])).pin_memory() for k in ("vx", "vy", "vz")]
+    hcell = torch.from_numpy(np.ascontiguousarray(wl["cell"], dtype=np.int32)).pin_memory()
+    res = []
+    for asynchronous in (False, True):
+        col = L.Collider.from_workload(wl, precision=L.F64, correction=0)
+        col.load_host(*(h.numpy() for h in host), hcell.numpy(), asynchronous=asynchronous)
+        col.step(wl["dt"], 0)
+        assert col.sync_code() == L.OK
+        res.append(col.moments())
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+
+    bad = hcell.clone()
+    bad[5] = wl["M"] + 3
+    col = L.Collider.from_workload(wl, precision=L.F64, correction=0)
+    col.load_host(*(h.numpy() for h in host), bad.numpy(), asynchronous=True)   # no error yet
+    col.collide_coulomb(wl["dt"], 0)
+    assert col.sync_code() == L.EINVAL
+    mom, _ = col.moments()
+    assert int(round(mom[:, 0].sum())) == len(wl["vx"]) - 1
