@@ -309,6 +309,18 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Hint: bring [p, p + bytes) into L2 (bulk prefetch; the range is widened to
+// 16-byte boundaries, which stay inside the 256-byte-aligned array).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~(uintptr_t)15;
+    for (uintptr_t q = a; q < e; q += 0x40000u) {   // chunks below the instruction's size limit
+        const uint32_t sz = (uint32_t)(e - q < 0x40000u ? e - q : 0x40000u);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(sz) : "memory");
+    }
+}
+
 // The null-collision candidate test U < P_null decided from the top 16 bits h
 // of the candidate word: the smallest uniform over all words with those bits
 // is below P_null exactly when h < H, with H computed here once per cell
@@ -646,6 +658,19 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         Cl<C>::sync();
 
         pc.mark(6);
+        // The next cell's id list into L2 now, and its first particle id, from
+        // which its velocity ranges are prefetched at the end of this cell.
+        // Rank 0 only: its s_item[par ^ 1] is complete here (its own copy, waited
+        // before the barrier above); the other CTAs of a cluster receive the
+        // item only at the end of the iteration.
+        uint32_t next_l0 = 0xFFFFFFFFu;
+        if (r == 0 && tid == 32u) {
+            const uint4 nx = s_item[par ^ 1u];
+            if (nx.w != 0u && nx.y != 0u) {
+                prefetch_l2(a.perm + nx.z, (size_t)nx.y * 4u);
+                next_l0 = a.perm[nx.z];
+            }
+        }
         // ---- 3. step S1: Takizuka-Abe collisions of pairs (2p, 2p+1), then the
         // optional restoration of the cell's momentum and energy.  The largest
         // squared speed after S1 is tracked for the null-collision bound.
@@ -931,6 +956,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         }
 
         pc.mark(9);
+        if (r == 0 && tid == 32u && next_l0 != 0xFFFFFFFFu) {   // cell-grouped storage: ids run from next_l0
+            const uint4 nx = s_item[par ^ 1u];
+            const uint32_t cnt = min(nx.y, a.n_cap - min(next_l0, a.n_cap));
+            prefetch_l2(a.vx + next_l0, (size_t)cnt * sizeof(T));
+            prefetch_l2(a.vy + next_l0, (size_t)cnt * sizeof(T));
+            prefetch_l2(a.vz + next_l0, (size_t)cnt * sizeof(T));
+        }
         // ---- 6. write velocities back through the id list (coalesced)
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {

@@ -149,6 +149,7 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     CellArgs<T> a;
     const Layout& L = ctx->L;
     a.vx = ctx->s<T>(L.vx); a.vy = ctx->s<T>(L.vy); a.vz = ctx->s<T>(L.vz);
+    a.n_cap = (uint32_t)ctx->cfg.capacity;
     a.perm = ctx->w<uint32_t>(L.perm);
     a.counts = ctx->w<uint32_t>(L.counts);
     a.cell_start = ctx->w<uint32_t>(L.cell_start);

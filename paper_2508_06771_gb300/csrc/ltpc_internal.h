@@ -44,6 +44,7 @@ struct DevState {
 template <class T>
 struct CellArgs {
     T* vx; T* vy; T* vz;
+    uint32_t n_cap;              // length of the particle arrays (capacity)
     const uint32_t* perm;        // particle ids grouped by cell (CCS3 output)
     const uint32_t* counts;      // N_j
     const uint32_t* cell_start;  // I_j
