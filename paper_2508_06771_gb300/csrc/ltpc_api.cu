@@ -289,10 +289,12 @@ int read_errors(ltpc_ctx* ctx)
 // Class tables: index lists into the compiled shapes of each precision.
 namespace ltpc {
 static const ClassTable kTabF32[] = {
-    {5, {0, 5, 6, 3, 4}},   // one CTA per cell up to 12288 (256/512/1024 threads), then clusters of 8
-    {5, {0, 1, 2, 3, 4}},   // 256-thread CTAs in clusters of 1/2/4/8
-    {2, {6, 4}},            // one 1024-thread CTA per cell up to 12288, then clusters of 8
-    {5, {0, 5, 7, 3, 4}},   // as table 0 with 512-thread CTAs (24 positions per thread) up to 12288
+    {6, {0, 5, 6, 8, 9, 4}},   // one CTA per cell up to 12288 (256/512/1024 threads), clusters of 2 and 4
+                               // 1024-thread CTAs up to 49152, then clusters of eight 512-thread CTAs
+    {5, {0, 5, 6, 3, 4}},      // one CTA per cell up to 12288, then clusters of 8 (256/512 threads)
+    {5, {0, 1, 2, 3, 4}},      // 256-thread CTAs in clusters of 1/2/4/8
+    {2, {6, 4}},               // one 1024-thread CTA per cell up to 12288, then clusters of 8
+    {5, {0, 5, 7, 3, 4}},      // as table 1 with 512-thread CTAs (24 positions per thread) up to 12288
 };
 static const ClassTable kTabF64[] = {
     {6, {0, 5, 6, 7, 3, 4}},   // one CTA per cell up to 6144, then clusters of 2/8

@@ -81,6 +81,44 @@ def test_grouping_and_pair_order_bit_exact(L, orc, prec):
     col.sync()
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_every_class_table_pairs_bit_exact(L, orc, prec):
+    """Every class table (every compiled block/cluster shape in use) gives the
+    oracle's pairing order bit for bit, and the same FP32 moments within 1e-5."""
+    counts = [3, 2049, 4097, 12289, 20000, 24577, 32769, 49153, 65536] if prec == "f32" else \
+        [3, 2049, 4097, 6145, 12289, 20000, 32768]
+    wl = big_cells_workload(counts, seed=8)
+    col = L.Collider.from_workload(wl, precision=L.F32 if prec == "f32" else L.F64)
+    col.load_workload(wl)
+    ocs, oorder = orc.pair_order(wl["cell"], wl["M"], wl["seed"], 7)
+    ref = None
+    tables = 0
+    for t in range(8):
+        try:
+            col.set_class_table(t)
+        except L.LtpcError as e:
+            assert e.code == L.EINVAL
+            break
+        tables += 1
+        gcs, gorder = col.pair_order(7)
+        assert np.array_equal(gcs.astype(np.uint64), ocs)
+        assert np.array_equal(gorder, oorder), t
+        col.load_workload(wl)
+        col.set_class_table(t)
+        col.collide_coulomb(wl["dt"], 0)        # Coulomb only: no discrete decisions to flip
+        mom, _ = col.moments()
+        if ref is None:
+            ref = mom
+        else:
+            np.testing.assert_array_equal(mom[:, 0], ref[:, 0])
+            s2 = ref[:, 5:8]                                          # sums of v_i^2
+            s1 = np.sqrt(ref[:, 0:1] * s2)                            # N v_rms per component
+            assert (np.abs(mom[:, 2:5] - ref[:, 2:5]) / s1).max() <= 1e-5, t
+            assert (np.abs(mom[:, 5:8] - s2) / s2).max() <= 1e-5, t
+    assert tables >= 2
+    col.sync()
+
+
 def test_pair_order_ragged_shuffled(L, orc):
     wl = W.ragged(M=41, mean_ppc=400, seed=9, shuffled=True)
     col = L.Collider.from_workload(wl, precision=L.F64)
