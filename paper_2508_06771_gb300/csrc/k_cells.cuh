@@ -239,14 +239,18 @@ __device__ __forceinline__ void for_each_masked(uint32_t* mask, uint32_t nw, uin
 }
 
 // Sum NQ per-thread partials over the cluster in a fixed order: warp
-// butterfly, then a second butterfly over the warps' partials (one warp per
-// quantity), both in the accumulator type; CTAs combined in rank order in
-// double.  Deterministic for a given block shape.
+// butterfly in the working precision (at most 32 x ITEMS values per warp
+// partial), then the warps' partials in double by one warp -- lane l takes
+// quantity l % NQ and every (32 / NQ)-th warp partial, summed as a tree, and
+// the lanes of a quantity are combined by xor shuffles -- and the CTAs in rank
+// order in double.  Deterministic for a given block shape.
 template <int NT, int C, int NQ, class A>
 __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, double* out)
 {
-    static_assert(NQ <= NT / 32, "one warp per quantity");
+    static_assert(32 % NQ == 0 && NQ <= NT / 32, "quantities per warp");
     constexpr int NW = NT / 32;
+    constexpr int G = 32 / NQ;                       // lanes per quantity
+    constexpr int PER = (NW + G - 1) / G;            // warp partials per lane
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
@@ -258,11 +262,23 @@ __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, 
         for (int k = 0; k < NQ; ++k) s_red[warp * NQ + k] = v[k];
     }
     __syncthreads();
-    if (warp < (unsigned)NQ) {
-        A x = lane < (unsigned)NW ? s_red[lane * NQ + warp] : A(0);
+    if (warp == 0) {
+        const unsigned k = lane % NQ, g = lane / NQ;
+        double x[PER];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-        if (lane == 0) s_cl[warp] = (double)x;
+        for (int i = 0; i < PER; ++i) {
+            const unsigned w = g + (unsigned)i * G;
+            x[i] = w < (unsigned)NW ? (double)s_red[w * NQ + k] : 0.0;
+        }
+#pragma unroll
+        for (int h = 1; h < PER; h <<= 1) {
+#pragma unroll
+            for (int i = 0; i + h < PER; i += 2 * h) x[i] += x[i + h];
+        }
+        double t = x[0];
+#pragma unroll
+        for (int o = NQ; o < 32; o <<= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        if (lane < (unsigned)NQ) s_cl[lane] = t;
     }
     Cl<C>::sync();
     if (threadIdx.x < (unsigned)NQ) {
@@ -743,7 +759,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             if (do_corr) {
                 cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
                 // V = c + S1 / n and K = S2 - |S1|^2 / n, before (0..3) and after (4..7)
-                if (tid < 7u) {   // restoration scalars, one per thread, in the working precision
+                if (tid < 7u) {   // restoration scalars from the double sums, in the working precision
+                    // (they scale binary32 velocities; a binary64 evaluation would be rounded away)
                     const T inv_n = T(1) / (T)n;
                     T val;
                     if (tid == 0) {
