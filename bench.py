@@ -5,7 +5,7 @@ Takizuka-Abe Coulomb + null-collision electron-neutral step + moments, fused
 per cell, replayed as a CUDA graph.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload cfg2|cfg1|cfg3|cfg4]
+                  [--workload tail_4096x10000|relax_64x1000|loguniform_256x256|instances_64]
 
 With N > 1 (torchrun), every rank runs an independent replica of the workload
 (its own seed): the method shards by cell and instance with no exchange, so
@@ -123,20 +123,20 @@ class ClockSampler:
 
 def make_workload(name, seed, rank=0, cells=None):
     from paper_2508_06771_gb300 import workloads as W
-    if name == "cfg2":
-        wl = W.cfg2(seed=seed, M=cells or 4096)
-        desc = f"cfg2: 1D grid of {wl['M']} cells x 10000 electrons (N0={wl['vx'].size:,}), FP32 SoA velocities, " \
+    if name == "tail_4096x10000":
+        wl = W.tail_4096x10000(seed=seed, M=cells or 4096)
+        desc = f"tail_4096x10000: 1D grid of {wl['M']} cells x 10000 electrons (N0={wl['vx'].size:,}), FP32 SoA velocities, " \
                "95% at 2 eV + 500/cell at 20 eV, Takizuka-Abe Coulomb + null-collision e-n (elastic, " \
                "ionization >15.76 eV), fused per-cell moments"
-    elif name == "cfg1":
-        wl = W.cfg1(seed=seed)
-        desc = "cfg1: 64 cells x 1000 electrons, FP64, anisotropic Maxwellian, Coulomb only"
-    elif name == "cfg3":
-        wl = W.cfg3(seed=seed, dtype=np.float32)
-        desc = f"cfg3: 256x256 cells, log-uniform 16..65536 per cell (N0={wl['vx'].size:,}), FP32, NRL lnL, Coulomb"
-    elif name == "cfg4":
-        wl = W.cfg4(seed=seed, dtype=np.float32)
-        desc = f"cfg4: 64 instances, {wl['M']} cells, N0={wl['vx'].size:,}, FP32, per-instance dt, Coulomb"
+    elif name == "relax_64x1000":
+        wl = W.relax_64x1000(seed=seed)
+        desc = "relax_64x1000: 64 cells x 1000 electrons, FP64, anisotropic Maxwellian, Coulomb only"
+    elif name == "loguniform_256x256":
+        wl = W.loguniform_256x256(seed=seed, dtype=np.float32)
+        desc = f"loguniform_256x256: 256x256 cells, log-uniform 16..65536 per cell (N0={wl['vx'].size:,}), FP32, NRL lnL, Coulomb"
+    elif name == "instances_64":
+        wl = W.instances_64(seed=seed, dtype=np.float32)
+        desc = f"instances_64: 64 instances, {wl['M']} cells, N0={wl['vx'].size:,}, FP32, per-instance dt, Coulomb"
     else:
         raise SystemExit(f"unknown workload {name}")
     return wl, desc
@@ -156,10 +156,10 @@ def run_reference(args, rank, world):
     from paper_2508_06771_gb300 import workloads as W
     orc.build()
     # calibrate the oracle's cost per particle on one small cell block
-    wl_small = W.cfg2(M=64, ppc=10000, seed=0, blocks=[0]) if args.workload == "cfg2" else None
-    if args.workload != "cfg2":
+    wl_small = W.tail_4096x10000(M=64, ppc=10000, seed=0, blocks=[0]) if args.workload == "tail_4096x10000" else None
+    if args.workload != "tail_4096x10000":
         wl_small = make_workload(args.workload, 0)[0]
-    full_wl_cells = 4096 if args.workload == "cfg2" else wl_small["M"]
+    full_wl_cells = 4096 if args.workload == "tail_4096x10000" else wl_small["M"]
     st = orc.State(wl_small)
     P = orc.make_params(wl_small, correction=True)
     neutral = wl_small.get("neutral", False)
@@ -171,9 +171,9 @@ def run_reference(args, rank, world):
     target = budget / nsteps / per_particle
     ppc = wl_small["vx"].size / wl_small["M"]
     cells = int(max(1, min(full_wl_cells, target // ppc)))
-    if args.workload == "cfg2":
+    if args.workload == "tail_4096x10000":
         blocks = list(range(max(1, (cells + W.BLOCK - 1) // W.BLOCK)))
-        wl = W.cfg2(seed=0, blocks=blocks)
+        wl = W.tail_4096x10000(seed=0, blocks=blocks)
         wl = W.subset_cells(wl, np.arange(min(cells, len(blocks) * W.BLOCK)))
     else:
         wl = W.subset_cells(wl_small, np.arange(min(cells, wl_small["M"])))
@@ -199,10 +199,10 @@ def run_reference(args, rank, world):
 
 
 def make_workload_desc(name):
-    return {"cfg2": "cfg2: 4096 cells x 10000 electrons, FP32 Coulomb + e-n null collision",
-            "cfg1": "cfg1: 64 cells x 1000 electrons, FP64 Coulomb",
-            "cfg3": "cfg3: 256x256 log-uniform cells, FP32 Coulomb",
-            "cfg4": "cfg4: 64 instances, FP32 Coulomb"}[name]
+    return {"tail_4096x10000": "tail_4096x10000: 4096 cells x 10000 electrons, FP32 Coulomb + e-n null collision",
+            "relax_64x1000": "relax_64x1000: 64 cells x 1000 electrons, FP64 Coulomb",
+            "loguniform_256x256": "loguniform_256x256: 256x256 log-uniform cells, FP32 Coulomb",
+            "instances_64": "instances_64: 64 instances, FP32 Coulomb"}[name]
 
 
 def cpu_baseline(workload, budget_s=12.0):
@@ -210,8 +210,8 @@ def cpu_baseline(workload, budget_s=12.0):
     import oracle as orc
     from paper_2508_06771_gb300 import workloads as W
     orc.build()
-    if workload == "cfg2":
-        wl = W.subset_cells(W.cfg2(seed=0, blocks=[0]), np.arange(16))
+    if workload == "tail_4096x10000":
+        wl = W.subset_cells(W.tail_4096x10000(seed=0, blocks=[0]), np.arange(16))
         wl["capacity"] = 2 * wl["vx"].size
         neutral = True
     else:
@@ -253,7 +253,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     # ---- the learned part: trained briefly on this workload's own particle data (another seed),
-    # then served in-loop every step and judged against the exact per-cell reduction
+    # then served in-loop every step and checked against the exact per-cell reduction
     from paper_2508_06771_gb300 import surrogate as SG
     net = ltpc.Surrogate(batch_max=4096, n_cells_max=wl["M"], seed=rank)
     sur = {"trained": False}
@@ -316,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
     ms_max, upd_all = float(t.item()), float(u.item())
     value = upd_all / (ms_max / 1e3)
     launches_per_step = 3 + len(classes) + 3      # scatter, cells per class, regroup, append; surrogate x3
-    # in-loop judge: surrogate rates of the last step against the exact particle reduction
+    # in-loop check: surrogate rates of the last step against the exact particle reduction
     _, exact = net.features(col, normalize=False)
     pred = net.infer(col)
     mi = exact[:, 0] > 0
@@ -477,9 +477,9 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--workload", default="tail_4096x10000", choices=["relax_64x1000", "tail_4096x10000", "loguniform_256x256", "instances_64"])
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--cells", type=int, default=None, help="cfg2 only: number of cells (profiling cases)")
+    ap.add_argument("--cells", type=int, default=None, help="tail_4096x10000 only: number of cells (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

@@ -6,7 +6,7 @@
 // thousands of particles per cell (Sec. 1).  The network maps a cell's binned
 // energy distribution (64 log bins) plus its density and mean energy to the
 // ionization and elastic rate coefficients; the exact particle reduction of the
-// cell kernel is both its training target and the judge of its error.
+// cell kernel is both its training target and the reference for its error.
 //
 // Kernels: feature extraction from the per-cell moments, one fused kernel per
 // 64-row tile for the forward pass and (when training) the backward pass with

@@ -75,7 +75,7 @@ def _assemble(M, counts, gen_block, seed, blocks=None, dtype=np.float64):
             np.concatenate(cells).astype(np.int32))
 
 
-def cfg1(M: int = 64, ppc: int = 1000, seed: int = 0, steps: int = 100) -> dict:
+def relax_64x1000(M: int = 64, ppc: int = 1000, seed: int = 0, steps: int = 100) -> dict:
     """Plain FP64 e-e Coulomb: anisotropic Maxwellian T_par = 2 eV (z), T_perp = 1 eV, n = 1e18,
     lnL = 10, dt = 0.1 / nu_e at T = (T_par + 2 T_perp)/3.  Each cell's sample is centred and
     rescaled so that its temperatures are exactly T_par and T_perp."""
@@ -99,7 +99,7 @@ def cfg1(M: int = 64, ppc: int = 1000, seed: int = 0, steps: int = 100) -> dict:
                  T_par=T_par, T_perp=T_perp, density=n, dt=dt)
 
 
-def cfg2(M: int = 4096, ppc: int = 10000, hot: int | None = None, seed: int = 0, steps: int = 1000,
+def tail_4096x10000(M: int = 4096, ppc: int = 10000, hot: int | None = None, seed: int = 0, steps: int = 1000,
          blocks=None) -> dict:
     """FP32 Coulomb + e-n: 95 % at 2 eV and 5 % (exactly `hot` per cell) at 20 eV, isotropic, zero
     drift; n_e = 3.22e21 (ionization fraction 0.1 of n_n); lnL = 10; dt fixed so that the
@@ -126,18 +126,18 @@ def cfg2(M: int = 4096, ppc: int = 10000, hot: int | None = None, seed: int = 0,
                  density=n_e, dt=dt, vmax0=vmax)
 
 
-def cfg3_counts(nx: int = 256, ny: int = 256, seed: int = 0) -> np.ndarray:
+def loguniform_counts(nx: int = 256, ny: int = 256, seed: int = 0) -> np.ndarray:
     """Per-cell counts floor(exp(U(ln 16, ln 65537))) on an nx x ny grid (cell id = ix + nx iy)."""
     rng = np.random.default_rng([seed, 999_999])
     return np.floor(np.exp(rng.uniform(math.log(16.0), math.log(65537.0), nx * ny))).astype(np.int64)
 
 
-def cfg3(nx: int = 256, ny: int = 256, seed: int = 0, steps: int = 200, blocks=None,
+def loguniform_256x256(nx: int = 256, ny: int = 256, seed: int = 0, steps: int = 200, blocks=None,
          dtype=np.float64) -> dict:
     """Uneven-cell batch: log-uniform counts in [16, 65536], isotropic 2 eV Maxwellian, density
     proportional to the count (1e18 m^-3 at 1024 particles), NRL lnL per cell, dt = 0.1/max nu_e."""
     M = nx * ny
-    counts = cfg3_counts(nx, ny, seed)
+    counts = loguniform_counts(nx, ny, seed)
     T = 2.0
 
     def gen(rng, cs):
@@ -155,7 +155,7 @@ def cfg3(nx: int = 256, ny: int = 256, seed: int = 0, steps: int = 200, blocks=N
                  nx=nx, ny=ny)
 
 
-def cfg4_layout(n_inst: int = 64, seed: int = 0):
+def instances_layout(n_inst: int = 64, seed: int = 0):
     """Instance sizes: cells U{64..4096}, particles per cell U{100..20000}, T U(0.5, 5) eV."""
     rng = np.random.default_rng([seed, 888_888])
     Mi = rng.integers(64, 4097, n_inst)
@@ -164,11 +164,11 @@ def cfg4_layout(n_inst: int = 64, seed: int = 0):
     return Mi, ppc, T
 
 
-def cfg4(n_inst: int = 64, seed: int = 0, steps: int = 100, instances=None, dtype=np.float64,
+def instances_64(n_inst: int = 64, seed: int = 0, steps: int = 100, instances=None, dtype=np.float64,
          scale_ppc: float = 1.0) -> dict:
     """Batch of independent plasma instances (disjoint cell ranges): n = 1e18, lnL = 10,
     dt_i = 0.1 / nu_e(T_i).  `instances` selects a subset (cells renumbered densely)."""
-    Mi, ppc, T = cfg4_layout(n_inst, seed)
+    Mi, ppc, T = instances_layout(n_inst, seed)
     ppc = np.maximum(2, (ppc * scale_ppc).astype(np.int64))
     sel = list(range(n_inst)) if instances is None else list(instances)
     n = 1e18

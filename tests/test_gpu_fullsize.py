@@ -82,22 +82,22 @@ def _check(L, orc, wl, cells, neutral, step=0):
     return worst
 
 
-def test_cfg2_full_size_sampled(L, orc):
-    wl = W.cfg2()                                      # 4096 cells x 10000, FP32, Coulomb + e-n
+def test_tail_4096x10000_full_size_sampled(L, orc):
+    wl = W.tail_4096x10000()                                      # 4096 cells x 10000, FP32, Coulomb + e-n
     for k in ("vx", "vy", "vz"):
         wl[k] = wl[k].astype(np.float32)
     cells = _sample_cells(np.full(wl["M"], 10000), 48, 1)
     _check(L, orc, wl, cells, neutral=True)
 
 
-def test_cfg3_full_size_sampled(L, orc):
-    wl = W.cfg3(dtype=np.float32)                      # 256x256 cells, 16..65536 per cell, NRL lnL
+def test_loguniform_256x256_full_size_sampled(L, orc):
+    wl = W.loguniform_256x256(dtype=np.float32)                      # 256x256 cells, 16..65536 per cell, NRL lnL
     cells = _sample_cells(wl["counts"], 120, 2)
     _check(L, orc, wl, cells, neutral=False)
 
 
-def test_cfg4_full_size_sampled(L, orc):
-    wl = W.cfg4(dtype=np.float32)                      # 64 instances, ~1.19e9 particles
+def test_instances_64_full_size_sampled(L, orc):
+    wl = W.instances_64(dtype=np.float32)                      # 64 instances, ~1.19e9 particles
     inst = wl["instance_of_cell"]
     counts = np.bincount(wl["cell"], minlength=wl["M"])
     rng = np.random.default_rng(3)

@@ -114,7 +114,7 @@ def test_training_reduces_loss(L):
 
 
 def test_surrogate_gain_over_direct_subsample(L):
-    """Trained on the particle method's own cfg2-like runs, the network predicts the
+    """Trained on the particle method's own tail_4096x10000-like runs, the network predicts the
     whole-cell ionization rate from 200-particle samples better than the direct
     estimate from the same samples (held-out run with another seed)."""
     import torch
@@ -122,14 +122,14 @@ def test_surrogate_gain_over_direct_subsample(L):
     M = 256
     net = L.Surrogate(batch_max=4096, n_cells_max=M, seed=0)
     S.identity_norm(net)
-    wl = W.cfg2(M=M, seed=0)
+    wl = W.tail_4096x10000(M=M, seed=0)
     col = L.Collider.from_workload(wl)
     col.load_workload(wl)
     X, T, _ = S.collect(col, net, wl["dt"], 0, 160, every=4, per_cells=(100, 200, 400, 1000, 0))
     Xn, Tn = S.fit_norm(net, X, T)
     S.train(net, Xn, Tn, epochs=25, batch=4096, lr=1e-3)
     # held-out run
-    wl1 = W.cfg2(M=M, seed=1)
+    wl1 = W.tail_4096x10000(M=M, seed=1)
     col1 = L.Collider.from_workload(wl1)
     col1.load_workload(wl1)
     col1.run(wl1["dt"], 0, 40)

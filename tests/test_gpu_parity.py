@@ -149,8 +149,8 @@ def _fp64_coulomb_case(L, orc, wl, steps=(0,)):
     return worst
 
 
-def test_fp64_coulomb_cfg1_reduced(L, orc):
-    wl = W.cfg1(M=16, ppc=1000)
+def test_fp64_coulomb_relax_reduced(L, orc):
+    wl = W.relax_64x1000(M=16, ppc=1000)
     _fp64_coulomb_case(L, orc, wl, steps=(0, 1, 2))
 
 
@@ -222,7 +222,7 @@ def _moment_errors(mom, omom, vth):
 
 
 def test_fp32_coulomb_moments(L, orc):
-    wl = W.cfg2(M=48, ppc=2000, steps=3)
+    wl = W.tail_4096x10000(M=48, ppc=2000, steps=3)
     wl["neutral"] = False
     v32 = [wl[k].astype(np.float32) for k in ("vx", "vy", "vz")]
     for k, v in zip(("vx", "vy", "vz"), v32):
@@ -244,7 +244,7 @@ def test_fp32_coulomb_moments(L, orc):
 
 
 def test_fp32_full_step_with_flip_accounting(L, orc):
-    wl = W.cfg2(M=32, ppc=2000, steps=1)
+    wl = W.tail_4096x10000(M=32, ppc=2000, steps=1)
     for k in ("vx", "vy", "vz"):
         wl[k] = wl[k].astype(np.float32).astype(np.float64)
     col = L.Collider.from_workload(wl, precision=L.F32)
@@ -272,7 +272,7 @@ def test_fp32_full_step_with_flip_accounting(L, orc):
 
 # ----------------------------------------------------------------------------- determinism, errors
 def test_determinism_graph_and_repeat(L):
-    wl = W.cfg2(M=16, ppc=3000, steps=1)
+    wl = W.tail_4096x10000(M=16, ppc=3000, steps=1)
     outs = []
     for use_graph in (True, True, False):
         col = L.Collider.from_workload(wl, precision=L.F32, use_graph=use_graph)

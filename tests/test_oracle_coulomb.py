@@ -109,7 +109,7 @@ def _temps(st, mass, charge):
 
 
 def test_coulomb_conservation_100_steps(orc):
-    wl = W.cfg1(M=8, ppc=1000)
+    wl = W.relax_64x1000(M=8, ppc=1000)
     P = orc.make_params(wl)
     st = orc.State(wl)
     p0, e0 = _cell_invariants(st, wl["M"])
@@ -136,7 +136,7 @@ def test_correction_restores_invariants(orc):
 
 
 def test_maxwellian_stationary(orc):
-    wl = W.cfg1(M=16, ppc=1000)
+    wl = W.relax_64x1000(M=16, ppc=1000)
     rng = np.random.default_rng(8)
     vt = math.sqrt(2.0 * W.E_CHARGE / W.M_E)
     for k in ("vx", "vy", "vz"):
@@ -182,15 +182,15 @@ def relaxation_reference(Tpar0, Tperp0, n, lnlam, times):
     return sol.y
 
 
-def test_nrl_rate_at_cfg1_start():
+def test_nrl_rate_at_relax_start():
     # Closed-form value quoted for the 2 eV / 1 eV, 1e18 m^-3, lnL = 10 case.
     assert math.isclose(nrl_isotropization_rate(2.0, 1.0, 1e18, 10.0), 5.06e6, rel_tol=2e-3)
 
 
 def _relaxation_rate_ratio(orc, div, M=256, t_end=53e-9, seed=0):
     """Fitted e-folding rate of T_par - T_perp over [0, t_end] divided by the NRL ODE's, at
-    dt = tau_e / div (tau_e = 1/nu_e of the cfg1 plasma)."""
-    wl = W.cfg1(M=M, seed=seed)
+    dt = tau_e / div (tau_e = 1/nu_e of the relax_64x1000 plasma)."""
+    wl = W.relax_64x1000(M=M, seed=seed)
     dt = wl["dt"] * 10.0 / div
     wl["dt_cell"] = np.full(M, dt)
     P = orc.make_params(wl)
@@ -214,7 +214,7 @@ def test_anisotropic_relaxation_rate(orc):
 
     Takizuka-Abe with a finite step under-relaxes: pairs slow enough that <delta^2> > 1 saturate
     at large angles, which removes a share of the rate that scales like (nu_e dt)^(1/3).  The rate
-    is measured at dt = tau_e/10 (the cfg1 step), tau_e/20 and tau_e/40, extrapolated linearly in
+    is measured at dt = tau_e/10 (the relax_64x1000 step), tau_e/20 and tau_e/40, extrapolated linearly in
     dt^(1/3) to dt -> 0, and that limit must equal the NRL rate.  A factor-2 error in the
     deflection variance would put the limit near 2."""
     divs = np.array([10.0, 20.0, 40.0])
@@ -223,4 +223,4 @@ def test_anisotropic_relaxation_rate(orc):
     x = (1.0 / divs) ** (1.0 / 3.0)
     slope, r0 = np.polyfit(x, r, 1)
     assert abs(r0 - 1.0) < 0.08, (r, r0)
-    assert 0.6 < r[0] < 0.9, r                        # the cfg1 step's known deficit
+    assert 0.6 < r[0] < 0.9, r                        # the relax_64x1000 step's known deficit
