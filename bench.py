@@ -149,51 +149,106 @@ def algorithmic_bytes_per_particle(prec):
 
 
 # ----------------------------------------------------------------------------- reference arm
+def oracle_sample(workload, cells=16):
+    """A few of the workload's cells, generated on their own (the oracle's inputs), and
+    whether the workload has the electron-neutral step."""
+    from paper_2508_06771_gb300 import workloads as W
+    blocks = list(range(max(1, (cells + W.BLOCK - 1) // W.BLOCK)))
+    if workload == "tail_4096x10000":
+        full = W.tail_4096x10000(seed=0, blocks=blocks)
+    elif workload == "relax_64x1000":
+        full = W.relax_64x1000(seed=0)
+    elif workload == "loguniform_256x256":
+        full = W.loguniform_256x256(seed=0, blocks=blocks)
+    else:
+        full = W.instances_64(seed=0, instances=[0])
+    wl = W.subset_cells(full, np.arange(min(cells, full["M"])))
+    wl["capacity"] = 2 * wl["vx"].size
+    return wl, bool(full.get("neutral", False))
+
+
+def _oracle_run(wl, neutral, warmup, steps, budget_s):
+    """The oracle as it stands on `wl` -- `steps` steps after `warmup`, or as many as fit
+    in `budget_s`.  Returns (particle-updates, seconds, steps)."""
+    import oracle as orc
+    st = orc.State(wl, capacity=wl["capacity"])
+    P = orc.make_params(wl, correction=True)
+    for k in range(warmup):
+        orc.step(st, P, k, True, neutral)
+    upd, done = 0, 0
+    t0 = time.perf_counter()
+    while (done < steps) if steps else (time.perf_counter() - t0 < budget_s):
+        upd += st.n
+        orc.step(st, P, warmup + done, True, neutral)
+        done += 1
+    return upd, time.perf_counter() - t0, done
+
+
+def oracle_rate(wl, neutral, warmup=0, steps=0, budget_s=8.0, processes=1):
+    """Particle-updates/s of the oracle on `wl`: in this process, or in `processes` worker
+    processes (this script with --oracle-worker; they load only numpy and the oracle), summed
+    over processes and divided by the slowest one's time."""
+    if processes <= 1:
+        res = [_oracle_run(wl, neutral, warmup, steps, budget_s)]
+    else:
+        import pickle
+        with tempfile.TemporaryDirectory() as td:
+            f = os.path.join(td, "sample.pkl")
+            with open(f, "wb") as fh:
+                pickle.dump({"wl": wl, "neutral": neutral, "warmup": warmup, "steps": steps,
+                             "budget_s": budget_s}, fh)
+            procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", f],
+                                      stdout=subprocess.PIPE, text=True) for _ in range(processes)]
+            res = []
+            for pr in procs:
+                out, _ = pr.communicate()
+                if pr.returncode != 0:
+                    raise RuntimeError(f"oracle worker failed ({pr.returncode})")
+                r = json.loads(out.strip().splitlines()[-1])
+                res.append((r["upd"], r["seconds"], r["steps"]))
+    upd = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return upd / el, el, min(r[2] for r in res)
+
+
+def oracle_worker(path):
+    import pickle
+    with open(path, "rb") as fh:
+        job = pickle.load(fh)
+    upd, el, done = _oracle_run(job["wl"], job["neutral"], job["warmup"], job["steps"], job["budget_s"])
+    print(json.dumps({"upd": upd, "seconds": el, "steps": done}), flush=True)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle as orc
-    from paper_2508_06771_gb300 import workloads as W
     orc.build()
-    # calibrate the oracle's cost per particle on one small cell block
-    wl_small = W.tail_4096x10000(M=64, ppc=10000, seed=0, blocks=[0]) if args.workload == "tail_4096x10000" else None
-    if args.workload != "tail_4096x10000":
-        wl_small = make_workload(args.workload, 0)[0]
-    full_wl_cells = 4096 if args.workload == "tail_4096x10000" else wl_small["M"]
-    st = orc.State(wl_small)
-    P = orc.make_params(wl_small, correction=True)
-    neutral = wl_small.get("neutral", False)
-    t0 = time.perf_counter()
-    orc.step(st, P, 0, True, neutral)
-    per_particle = (time.perf_counter() - t0) / max(1, st.n)
-    budget = 150.0
+    cores = host_cores()
+    # size the sample so that every process's warm-up + timed steps take ~2 minutes in all
+    wl1, neutral = oracle_sample(args.workload, cells=16)
+    v1, _, _ = oracle_rate(wl1, neutral, steps=1)
+    per_particle = 1.0 / v1
     nsteps = args.steps + args.warmup
-    target = budget / nsteps / per_particle
-    ppc = wl_small["vx"].size / wl_small["M"]
-    cells = int(max(1, min(full_wl_cells, target // ppc)))
-    if args.workload == "tail_4096x10000":
-        blocks = list(range(max(1, (cells + W.BLOCK - 1) // W.BLOCK)))
-        wl = W.tail_4096x10000(seed=0, blocks=blocks)
-        wl = W.subset_cells(wl, np.arange(min(cells, len(blocks) * W.BLOCK)))
-    else:
-        wl = W.subset_cells(wl_small, np.arange(min(cells, wl_small["M"])))
-    st = orc.State(wl, capacity=2 * wl["vx"].size)
-    P = orc.make_params(wl, correction=True)
-    for s in range(args.warmup):
-        orc.step(st, P, s, True, neutral)
-    upd = 0
-    t0 = time.perf_counter()
-    for s in range(args.warmup, args.warmup + args.steps):
-        upd += st.n
-        orc.step(st, P, s, True, neutral)
-    el = time.perf_counter() - t0
-    v = upd / el
-    sample = f"{wl['M']} of the workload's cells ({st.n:,} particles), {args.steps} steps, FP64 oracle, 1 thread"
+    target = 120.0 / nsteps / per_particle
+    ppc = wl1["vx"].size / wl1["M"]
+    cells = int(max(1, min(512, target // ppc)))   # at most ~5M particles per process
+    wl, neutral = oracle_sample(args.workload, cells=cells)
+    v, el, _ = oracle_rate(wl, neutral, warmup=args.warmup, steps=args.steps, processes=cores)
+    sample = (f"{wl['M']} of the workload's cells ({wl['vx'].size:,} particles) per process, {args.steps} steps "
+              f"after {args.warmup} warm-up, FP64 oracle, {cores} processes (one per host core)")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": make_workload_desc(args.workload)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -205,31 +260,19 @@ def make_workload_desc(name):
             "instances_64": "instances_64: 64 instances, FP32 Coulomb"}[name]
 
 
-def cpu_baseline(workload, budget_s=12.0):
-    """The oracle as it stands on a bounded sample of the workload (rank 0, N=1)."""
+def cpu_baseline(workload, budget_s=8.0):
+    """The oracle as it stands on a bounded sample of the workload (rank 0, N=1), on one core
+    and on every host core (one process per core)."""
     import oracle as orc
-    from paper_2508_06771_gb300 import workloads as W
     orc.build()
-    if workload == "tail_4096x10000":
-        wl = W.subset_cells(W.tail_4096x10000(seed=0, blocks=[0]), np.arange(16))
-        wl["capacity"] = 2 * wl["vx"].size
-        neutral = True
-    else:
-        full = make_workload(workload, 0)[0]
-        wl = W.subset_cells(full, np.arange(min(full["M"], 16)))
-        neutral = full.get("neutral", False)
-    st = orc.State(wl)
-    P = orc.make_params(wl, correction=True)
-    upd, s = 0, 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        upd += st.n
-        orc.step(st, P, s, True, neutral)
-        s += 1
-    el = time.perf_counter() - t0
-    return {"value": upd / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{wl['M']} cells ({wl['vx'].size:,} particles) of the workload, {s} full steps "
-                      f"(Coulomb{' + e-n' if neutral else ''} + moments), FP64, single thread, {el:.1f} s"}
+    wl, neutral = oracle_sample(workload, cells=16)
+    v1, el1, s1 = oracle_rate(wl, neutral, budget_s=budget_s)
+    cores = host_cores()
+    vn, eln, sn = oracle_rate(wl, neutral, budget_s=budget_s, processes=cores) if cores > 1 else (v1, el1, s1)
+    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle", "single_core": v1,
+            "sample": f"{wl['M']} cells ({wl['vx'].size:,} particles) of the workload per process, full steps "
+                      f"(Coulomb{' + e-n' if neutral else ''} + moments), FP64; {cores} processes x {sn} steps "
+                      f"in {eln:.1f} s, and 1 process x {s1} steps in {el1:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -487,7 +530,11 @@ def main():
     ap.add_argument("--train-steps", type=int, default=1024)
     ap.add_argument("--train-every", type=int, default=16)
     ap.add_argument("--train-epochs", type=int, default=8)
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
