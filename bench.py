@@ -363,8 +363,12 @@ def run_ours(args, rank, world, local_rank):
     _, exact = net.features(col, normalize=False)
     pred = net.infer(col)
     mi = exact[:, 0] > 0
-    sur["k_ion_rel_err_median"], sur["k_ion_rel_err_mean"] = SG.relative_errors(pred[:, 0], exact[:, 0], mi)
-    sur["k_el_rel_err_median"], sur["k_el_rel_err_mean"] = SG.relative_errors(pred[:, 1], exact[:, 1])
+    if sur["trained"] and bool(mi.any()):
+        sur["k_ion_rel_err_median"], sur["k_ion_rel_err_mean"] = SG.relative_errors(pred[:, 0], exact[:, 0], mi)
+        sur["k_el_rel_err_median"], sur["k_el_rel_err_mean"] = SG.relative_errors(pred[:, 1], exact[:, 1])
+    else:
+        sur["errors"] = None
+        sur["why"] = "not trained in this run" if not sur["trained"] else "no electron-neutral collisions in this workload"
     sur["served"] = "every step, all cells (features from the fused moments, BF16 MLP, rates)"
 
     # ---- per-kernel device times (CUDA events on the launching stream) for the roofline
@@ -378,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
     names = ["scatter"] + [f"cells_C{c['cluster']}x{c['threads']}" for c in classes] + ["regroup", "append"]
     dom = int(np.argmax(avg))
     n_now = col.count()
-    # cells of cfg-like workloads fall in one class; count the particles that class processes
+    # count the particles the dominant class processes
     counts = col.grouping()[2].astype(np.int64) if dom not in (0, len(names) - 2, len(names) - 1) else None
     if counts is not None:
         k = dom - 1
@@ -395,9 +399,16 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- FP64 plain form on the same workload (no graph), for the FP32-vs-FP64 comparison
     fp64 = None
+    colD = None
     if prec == "f32" and not args.no_fp64:
         colD = ltpc.Collider.from_workload(wl, precision=ltpc.F64, use_graph=False)
-        colD.load_workload(wl)
+        try:
+            colD.load_workload(wl)
+        except ltpc.LtpcError as e:       # e.g. cells above the binary64 shapes' capacity
+            fp64 = {"unavailable": str(e)}
+            colD.close()
+            colD = None
+    if colD is not None:
         colD.run(dt, 0, 2)
         colD.sync()
         ns = max(3, min(10, args.steps // 10))
@@ -415,7 +426,7 @@ def run_ours(args, rank, world, local_rank):
                 "steps": ns, "form": "same kernels in binary64, one launch per class, no graph, no correction"}
         fp64["fp32_speedup"] = value / world / fp64["value"]
         colD.close()
-        del colD
+        colD = None
         torch.cuda.empty_cache()
 
     # ---- end to end through the C ABI: host buffers in, moments out, every step.
