@@ -219,6 +219,20 @@ def oracle_worker(path):
     print(json.dumps({"upd": upd, "seconds": el, "steps": done}), flush=True)
 
 
+def reduce_over_ranks(elapsed, units, world, device="cpu"):
+    """Whole-job timing of a weak-scaling run: the slowest rank's time and the units all
+    ranks processed (every rank runs its own replica; the timed region ends in a barrier)."""
+    if world <= 1:
+        return float(elapsed), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -351,12 +365,7 @@ def run_ours(args, rank, world, local_rank):
     col.sync()
     n_end = col.count()
     updates = args.steps * (n_start + n_end) / 2.0      # particle count grows ~linearly through the run
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    u = torch.tensor([updates], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    ms_max, upd_all = float(t.item()), float(u.item())
+    ms_max, upd_all = reduce_over_ranks(ms, updates, world, "cuda")
     value = upd_all / (ms_max / 1e3)
     launches_per_step = 3 + len(classes) + 3      # scatter, cells per class, regroup, append; surrogate x3
     # in-loop check: surrogate rates of the last step against the exact particle reduction
@@ -473,14 +482,9 @@ def run_ours(args, rank, world, local_rank):
         el = time.perf_counter() - t0
         for c_ in (col, col2):
             c_.sync()                             # deferred load errors, if any
-        upd_e = ne * n0
-        te = torch.tensor([el], dtype=torch.float64, device="cuda")
-        ue = torch.tensor([float(upd_e)], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            dist.all_reduce(ue, op=dist.ReduceOp.SUM)
+        el_max, upd_e = reduce_over_ranks(el, ne * n0, world, "cuda")
         es = 4 if prec == "f32" else 8
-        e2e = {"value": float(ue.item()) / float(te.item()), "unit": UNIT,
+        e2e = {"value": upd_e / el_max, "unit": UNIT,
                "h2d_bytes_per_step": int(n0 * (3 * es + 4)),
                "d2h_bytes_per_step": int(wl["M"] * (10 * 8 + 64 * 4)), "steps": ne,
                "ms_per_step": el / ne * 1e3,
