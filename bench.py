@@ -304,8 +304,9 @@ def run_ours(args, rank, world, local_rank):
     dt = col.dt
     col.load_workload(wl)
     n0 = col.count()
-    if args.autotune:
-        col.autotune(dt)
+    table = 0
+    if not args.no_autotune:              # class table (block/cluster shapes) chosen by measurement
+        table = col.autotune(dt)
     classes = col.classes()
     stream = torch.cuda.current_stream()
 
@@ -450,6 +451,7 @@ def run_ours(args, rank, world, local_rank):
         hn = [h.numpy() for h in host]
         s2 = torch.cuda.Stream()
         col2 = ltpc.Collider.from_workload(wl, precision=col.precision, stream=s2)
+        col2.set_class_table(table)
         net2 = ltpc.Surrogate(batch_max=4096, n_cells_max=wl["M"], seed=rank)
         net2.set_params(net.get_params())
         net2.set_norm(*net.norm)
@@ -511,6 +513,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (
                            n0 * (16 if prec == 'f32' else 28) / 1e6),
                        "class_table": [f"C={c['cluster']} x {c['threads']} thr, cells<={c['max_n']}" for c in classes],
+                       "class_table_index": table, "autotuned": not args.no_autotune,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": names[dom],
@@ -536,7 +539,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tail_4096x10000", choices=["relax_64x1000", "tail_4096x10000", "loguniform_256x256", "instances_64"])
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default class table")
     ap.add_argument("--cells", type=int, default=None, help="tail_4096x10000 only: number of cells (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
