@@ -461,7 +461,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     const uint32_t list_n = ds->class_n[a.cls];
     const uint32_t step = ds->step;
     const double dt = ds->dt;
-    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const bool do_coul = (a.flags & F_COULOMB) != 0u;
     const bool do_neut = (a.flags & F_NEUTRAL) != 0u;
     const bool do_corr = (a.flags & F_CORRECTION) != 0u;
@@ -532,7 +531,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             hp[i] = 0u;
             if (k < nh) {
                 const uint32_t l = hl[i];
-                const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
+                const uint4 rw = draw(a.keys, l, step, TAG_PARTICLE);
                 const uint32_t b = __umulhi(rw.x, nb);
                 uint32_t b0;
                 const uint32_t ro = BB.locate(b, b0);
@@ -745,7 +744,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     T bx = X.y, by = Y.y, bz = Z.y;
                     const uint2 L2 = *reinterpret_cast<const uint2*>(sl + ia);
                     if (do_corr) presum(bx, by, bz, 0);
-                    const uint4 w = draw(k0, k1, L2.x < L2.y ? L2.x : L2.y, step, TAG_PAIR);
+                    const uint4 w = draw(a.keys, L2.x < L2.y ? L2.x : L2.y, step, TAG_PAIR);
                     ta_collide<T>(ax, ay, az, bx, by, bz, A, w);
                     *reinterpret_cast<V2*>(svx + ia) = Vec2<T>::make(ax, bx);
                     *reinterpret_cast<V2*>(svy + ia) = Vec2<T>::make(ay, by);
@@ -842,7 +841,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             bool ionized = false;
             auto collide = [&](uint32_t q) {
                 const uint32_t l = sl[q];
-                const uint4 rw = draw(k0, k1, l, step, TAG_PARTICLE);
+                const uint4 rw = draw(a.keys, l, step, TAG_PARTICLE);
                 if (!(unif<T>(rw.y) < pnull)) return;
                 const T x = svx[q], y = svy[q], z = svz[q];
                 const T v2 = x * x + y * y + z * z;
@@ -852,7 +851,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const T nu_ion = E >= e_ion ? nsion * v : T(0);
                 const T rr = unif<T>(rw.z) * numax;
                 if (rr < nu_el) {                              // C1: elastic, cold heavy target
-                    const uint4 sc = draw(k0, k1, l, step, TAG_SCATTER);
+                    const uint4 sc = draw(a.keys, l, step, TAG_SCATTER);
                     T dx, dy, dz;
                     iso_dir<T>(sc.x, sc.y, dx, dy, dz);
                     const T cchi = (x * dx + y * dy + z * dz) * Math<T>::rcp(v);
@@ -934,8 +933,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     const uint32_t rank = ion_base + s_ioff[q >> 5] + (uint32_t)__popc(s_imask[q >> 5] & ((1u << (q & 31u)) - 1u));
                     const T x = svx[q], y = svy[q], z = svz[q];
                     const T E = (x * x + y * y + z * z) * half_m_over_e;
-                    const uint4 sc = draw(k0, k1, l, step, TAG_SCATTER);
-                    const uint4 sd = draw(k0, k1, l, step, TAG_SECONDARY);
+                    const uint4 sc = draw(a.keys, l, step, TAG_SCATTER);
+                    const uint4 sd = draw(a.keys, l, step, TAG_SECONDARY);
                     const T Ep = E - e_ion;
                     const T Es = unif<T>(sc.z) * Ep;
                     const T vp = M::sqrt(two_e_over_m * (Ep - Es)), vs = M::sqrt(two_e_over_m * Es);

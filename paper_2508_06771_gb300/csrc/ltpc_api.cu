@@ -166,6 +166,7 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.cls = 0;
     a.flags = flags;
     a.seed = ctx->cfg.seed;
+    a.keys = philox_keys(ctx->cfg.seed);
     a.coef0 = ctx->coef0;
     a.weight = ctx->cfg.weight;
     a.mass = ctx->cfg.mass;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "philox.cuh"
+
 namespace ltpc {
 
 // Device-detected error bits (reported by ltpc_sync as LTPC_E* codes).
@@ -61,6 +63,7 @@ struct CellArgs {
     uint32_t cls;
     uint32_t flags;
     uint64_t seed;
+    PhiloxKeys keys;             // round keys of the seed
     double coef0;                // q^4 w / (8 pi eps0^2 mu^2), mu = m/2
     double weight, mass, e_over_m;
     double n_neutral, sigma_el, sigma_ion, e_ion, mratio2;  // mratio2 = 2 m / M
