@@ -40,7 +40,7 @@ extern "C" {
 #define LTPC_EINVAL (-1)       /* bad argument or configuration            */
 #define LTPC_ECAPACITY (-2)    /* ionization would exceed the capacity     */
 #define LTPC_ECUDA (-3)        /* a CUDA runtime call failed               */
-#define LTPC_ETIMEOUT (-4)     /* a bounded device-side wait gave up       */
+#define LTPC_ETIMEOUT (-4)     /* reserved: no entry point waits on the device */
 #define LTPC_ENONFINITE (-5)   /* a loaded velocity is NaN or infinite     */
 #define LTPC_EUNSUPPORTED (-6) /* a cell is larger than the largest class  */
 #define LTPC_EINTERNAL (-7)    /* an internal bounds check failed          */
@@ -111,8 +111,8 @@ void ltpc_destroy(ltpc_ctx* ctx);
  * moments of the loaded state.
  * Synchronizing by default.  Errors: EINVAL (n < 0, n > capacity or unknown
  * flags), ECUDA; ENONFINITE and EINVAL for cell ids out of range are reported
- * by this call, or with LTPC_LOAD_ASYNC by the next ltpc_sync / ltpc_moments
- * (particles with bad cell ids are then left out of the grouping; host
+ * by this call, or with LTPC_LOAD_ASYNC by the next ltpc_sync (particles
+ * with bad cell ids are then left out of the grouping; host
  * sources must stay unchanged until the stream reaches the copy). */
 int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const void* x,
                         const void* vx, const void* vy, const void* vz, int flags);
@@ -184,11 +184,14 @@ int ltpc_grouping(ltpc_ctx* ctx, uint32_t* d_cell_start, uint32_t* d_perm, uint3
 int ltpc_classes(ltpc_ctx* ctx, int32_t* n_classes, int32_t* cluster, int32_t* threads,
                  int32_t* per_cta, int32_t* max_n);
 
-/* Choose among the compiled class tables by timing one pass of each on the
- * loaded particles (particles are restored afterwards).  The choice changes
+/* Choose among the compiled class tables by timing collision-free passes
+ * (grouping, ordering, staging and moments; the particles are not changed)
+ * of each on the loaded particles.  The choice changes
  * only the schedule; the per-cell arithmetic may round differently between
  * tables (reductions follow the CTA shape).  Synchronizing. */
 int ltpc_autotune(ltpc_ctx* ctx, double dt, int32_t* chosen_table);
+/* Select class table `table` (0 = default) and rebuild the work lists for
+ * the current counts.  Synchronizing.  Errors: EINVAL for an unknown table. */
 int ltpc_set_class_table(ltpc_ctx* ctx, int32_t table);
 
 /* ---- rate-coefficient surrogate --------------------------------------------
