@@ -79,7 +79,11 @@ typedef struct ltpc_config {
     const double* inv_volume;   /* host [M]: 1/V_j                             */
     const double* dt_factor;    /* host [M] or NULL (all 1)                    */
     const double* lnlambda;     /* host [M] or NULL (all 10); constant mode    */
-    int32_t reserved[8];        /* must be zero                                */
+    int32_t cache_grouping;     /* 1: skip the per-step CCS3 scatter while no
+                                   particle was loaded or appended since the
+                                   last one (particles never change cells in
+                                   this library); 0: group every step          */
+    int32_t reserved[7];        /* must be zero                                */
 } ltpc_config;
 
 /* Bytes of the two caller-owned device buffers for `cfg`.

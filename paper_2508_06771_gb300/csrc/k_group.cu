@@ -29,13 +29,15 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
 }
 
 // CCS3: perm[I_j + rank] = l.  Cell ids outside [0, M) are skipped (the load's
-// histogram reports them).  Each warp takes 128 consecutive particles (4 per
+// histogram reports them).  With the cached-grouping option the kernel exits
+// at once while the previous grouping still holds.  Each warp takes 128 consecutive particles (4 per
 // lane, 16-byte loads).  When they all belong to one cell -- the usual case for
 // cell-grouped storage -- one cursor atomic serves the 128 and the ids are
 // written with 16-byte stores; otherwise one atomic per warp and cell.
 static __global__ void k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
                                  uint32_t* __restrict__ perm, const DevState* __restrict__ ds)
 {
+    if (ds->grouping_valid) return;                  // cached grouping: perm is current
     const unsigned long long n = ds->n;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
@@ -223,6 +225,8 @@ k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_
     if (tid == 0) {
         ds->max_count = s_max;
         ds->n_ion = total_ion;
+        // after a pass that appended nothing the grouping of the next pass is this one's
+        ds->grouping_valid = (lists.cache_grouping && append && total_ion == 0u) ? 1u : 0u;
         ds->n += total_ion;
         if (advance_step) ds->step += 1u;
     }
@@ -259,7 +263,7 @@ static __global__ void k_append(int32_t M, const uint32_t* __restrict__ ion_off,
 
 static __global__ void k_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step)
 {
-    if (set_n) { ds->n = n; ds->n_ion = 0u; }
+    if (set_n) { ds->n = n; ds->n_ion = 0u; ds->grouping_valid = 0u; }
     if (set_step) { ds->step = step; ds->dt = dt; }
 }
 

@@ -126,6 +126,7 @@ int set_table(ltpc_ctx* ctx, int table)
     ctx->kernel_idx.assign(T.kernel, T.kernel + T.n);
     ctx->grid.assign(T.n, 0);
     ctx->lists.n_classes = T.n;
+    ctx->lists.cache_grouping = ctx->cfg.cache_grouping;
     for (int k = 0; k < MAX_CLASSES; ++k) {
         ctx->lists.max_n[k] = 0;
         ctx->lists.list[k] = ctx->w<uint4>(ctx->L.lists) + (size_t)k * ctx->cfg.n_cells;
@@ -347,7 +348,8 @@ int ltpc_create(ltpc_ctx** out, const ltpc_config* cfg, void* d_state, void* d_w
     if (!cfg->inv_volume || !(cfg->mass > 0) || !(cfg->charge > 0) || !(cfg->eps0 > 0) || !(cfg->weight > 0))
         return LTPC_EINVAL;
     if (cfg->lnlambda_mode != LTPC_LNL_CONST && cfg->lnlambda_mode != LTPC_LNL_NRL) return LTPC_EINVAL;
-    for (int i = 0; i < 8; ++i)
+    if (cfg->cache_grouping != 0 && cfg->cache_grouping != 1) return LTPC_EINVAL;
+    for (int i = 0; i < 7; ++i)
         if (cfg->reserved[i]) return LTPC_EINVAL;
     ltpc_ctx* ctx = new (std::nothrow) ltpc_ctx();
     if (!ctx) return LTPC_EINVAL;

@@ -40,6 +40,7 @@ struct DevState {
     unsigned int ticket[MAX_CLASSES]; // dynamic work counters, reset every step
     unsigned int n_ion;               // secondaries appended by the last pass
     unsigned int max_count;           // largest cell at the last regrouping
+    unsigned int grouping_valid;      // 1: perm still groups the particles (no load, no append since)
 };
 
 // Arguments of the cell kernel (one cluster per cell).

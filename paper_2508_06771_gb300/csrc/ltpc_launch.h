@@ -14,6 +14,7 @@ struct RegroupLists {
     int32_t n_classes;
     uint32_t max_n[MAX_CLASSES];   // largest cell of each class
     uint4* list[MAX_CLASSES];      // device work lists (M entries each): {cell, N_j, I_j, 1}
+    int32_t cache_grouping;        // 1: skip CCS3 while the grouping is unchanged
 };
 
 // One compiled shape of the cell kernel.

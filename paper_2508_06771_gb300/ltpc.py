@@ -43,7 +43,7 @@ class Config(C.Structure):
         ("lnlambda_mode", C.c_int32), ("correction", C.c_int32), ("has_position", C.c_int32),
         ("use_graph", C.c_int32),
         ("inv_volume", C.POINTER(C.c_double)), ("dt_factor", C.POINTER(C.c_double)),
-        ("lnlambda", C.POINTER(C.c_double)), ("reserved", C.c_int32 * 8),
+        ("lnlambda", C.POINTER(C.c_double)), ("cache_grouping", C.c_int32), ("reserved", C.c_int32 * 7),
     ]
 
 
@@ -122,7 +122,8 @@ class Collider:
                  mass: float, charge: float, eps0: float, weight: float = 1.0, n_neutral: float = 0.0,
                  mass_neutral: float = 1.0, sigma_el: float = 0.0, sigma_ion: float = 0.0, e_ion: float = 1e30,
                  lnlambda_mode: int = LNL_CONST, correction: int = -1, has_position: bool = False,
-                 use_graph: bool = True, dt_factor=None, lnlambda=None, device=None, stream=None):
+                 use_graph: bool = True, dt_factor=None, lnlambda=None, device=None, stream=None,
+                 cache_grouping: bool = False):
         import torch
 
         self.torch = torch
@@ -146,6 +147,7 @@ class Collider:
             n_neutral, mass_neutral, sigma_el, sigma_ion, e_ion)
         cfg.lnlambda_mode, cfg.correction = lnlambda_mode, correction
         cfg.has_position, cfg.use_graph = int(bool(has_position)), int(bool(use_graph))
+        cfg.cache_grouping = int(bool(cache_grouping))
         cfg.inv_volume = _f64p(self._inv)
         cfg.dt_factor = _f64p(self._dtf) if self._dtf is not None else None
         cfg.lnlambda = _f64p(self._lnl) if self._lnl is not None else None

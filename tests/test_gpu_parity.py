@@ -334,3 +334,25 @@ def test_async_load_matches_sync_and_defers_errors(L):
     assert col.sync_code() == L.EINVAL
     mom, _ = col.moments()
     assert int(round(mom[:, 0].sum())) == len(wl["vx"]) - 1
+
+
+@pytest.mark.parametrize("neutral", [False, True])
+def test_cached_grouping_identical(L, orc, neutral):
+    """cache_grouping skips CCS3 while nothing was loaded or appended; the results are
+    bit-identical to grouping every step (with appends the grouping is redone)."""
+    wl = W.ragged(M=21, mean_ppc=400, seed=17, shuffled=True, T_eV=14.0)
+    wl["dt_cell"] = np.full(wl["M"], 3e-11)
+    wl["neutral"] = neutral
+    out = []
+    for cache in (False, True):
+        col = L.Collider.from_workload(wl, precision=L.F64, correction=0, cache_grouping=cache)
+        col.load_workload(wl)
+        col.run(col.dt, 0, 4)
+        mom, hist = col.moments()
+        out.append((mom, hist, col.read()))
+        assert col.sync_code() == L.OK
+    (m0, h0, r0), (m1, h1, r1) = out
+    np.testing.assert_array_equal(m0, m1)
+    np.testing.assert_array_equal(h0, h1)
+    for a, b in zip(r0[:4], r1[:4]):
+        np.testing.assert_array_equal(a, b)
