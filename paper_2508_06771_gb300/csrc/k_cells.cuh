@@ -13,7 +13,13 @@
 //      (Table 3, CS5) at a deterministic slot;
 //   4. the particle-to-cell moments of steps S3a/S3b (Sec. 4.5) of the result.
 // Velocities are read once from HBM (gathered through the cell's index list,
-// CCS3) and written once.  Index math is in ltpc_index.h.
+// CCS3) and written once.  Latency hiding: the next work item is drawn one
+// ticket ahead and copied with cp.async, the cell's parameters are prefetched
+// the same way, single-CTA classes gather the velocities with cp.async
+// straight into pairing order, and the next cell's id list and velocity
+// ranges are brought into L2 while the current cell computes.  Per-cell sums
+// are formed per thread and per warp in the working precision and combined in
+// double.  Index math is in ltpc_index.h.
 #pragma once
 #include <cooperative_groups.h>
 
