@@ -72,7 +72,7 @@ template <> struct Math<float> {
     }
     static __device__ __forceinline__ float ln(float x) { return __logf(x); }
     static __device__ __forceinline__ float expm1(float x) { return expm1f(x); }
-    // sin and cos of 2 pi u for u in (0, 1], evaluated on (-pi, pi]
+    // sin and cos of 2 pi u for u in [0, 1], evaluated on [-pi, pi]
     static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c)
     {
         float sx, cx;
@@ -82,12 +82,12 @@ template <> struct Math<float> {
     }
     static __device__ __forceinline__ int ebin(float E)
     {
-        if (!(E > 0.f)) return 0;
-        const float t = fmaf(__log2f(E), 0.30102999566398120f * 12.8f, 25.6f);   // (log10 E + 2) 64/5
-        if (!(t >= 0.f)) return 0;
-        if (t >= 63.f) return 63;
-        // floor(t) for 0 <= t < 2^23 without a float-to-integer conversion: t + 2^23
-        // rounded down has floor(t) as its low mantissa bits
+        // (log10 E + 2) 64/5 clamped to [0, 63] (E = 0, subnormal or NaN: log2 gives
+        // -inf or NaN, which fmaxf maps to 0), then its floor without a
+        // float-to-integer conversion: t + 2^23 rounded down has floor(t) as its low
+        // mantissa bits
+        float t = fmaf(__log2f(E), 0.30102999566398120f * 12.8f, 25.6f);
+        t = fminf(fmaxf(t, 0.f), 63.f);
         return (int)(__float_as_uint(__fadd_rd(t, 8388608.0f)) & 0x7FFFFFu);
     }
 };
@@ -123,8 +123,8 @@ __device__ __forceinline__ void ta_collide(T& ax, T& ay, T& az, T& bx, T& by, T&
     const T iu = M::rcp(u);
     const T var = A * iu * iu * iu;
     T sth, cth, sph, cph;
-    M::sincos2pi(unif<T>(w.y), &sth, &cth);
-    M::sincos2pi(unif<T>(w.z), &sph, &cph);
+    M::sincos2pi(unif_angle<T>(w.y), &sth, &cth);
+    M::sincos2pi(unif_angle<T>(w.z), &sph, &cph);
     const T delta = M::sqrt(var * (T(-2) * M::ln(unif<T>(w.x)))) * cth;
     // sin(Theta) = 2d/(1+d^2), 1-cos(Theta) = 2d^2/(1+d^2); for |d| > 1 use t = 1/d
     const bool small = fabs(delta) <= T(1);
@@ -211,8 +211,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_scan
     __syncthreads();
     const uint32_t res = s_scan[warp] + x - v;
     *total = s_scan[NT / 32];
-    __syncthreads();
-    return res;
+    return res;   // callers pass a barrier before s_scan is written again
 }
 
 constexpr uint32_t LISTCAP = 512;    // positions handled per round of a masked pass
@@ -395,6 +394,18 @@ struct Bounds {
     }
 };
 
+// Scalar k of the cell's record in the working precision: 0 = A, 1 = dt,
+// 2..4 = mean velocity (binary32 copies made with the record; binary64 as is).
+template <class T> __device__ __forceinline__ T cell_scalar(const double* cp, int k);
+template <> __device__ __forceinline__ float cell_scalar<float>(const double* cp, int k)
+{
+    return reinterpret_cast<const float*>(cp + CP_F32)[k];
+}
+template <> __device__ __forceinline__ double cell_scalar<double>(const double* cp, int k)
+{
+    return cp[k == 0 ? CP_A : k == 1 ? CP_DT : CP_C + (k - 2)];
+}
+
 // Shared-memory bytes a launch of the cell kernel needs (dynamic part).
 template <class T>
 __host__ __device__ constexpr size_t cells_dyn_smem(uint32_t capl)
@@ -440,11 +451,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     // candidate words: by home index during the sort, by position afterwards;
     // 16 bytes past the sort view's bucket counters, so the sort never overlaps it
     uint16_t* sw = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(sl + CAPL) + 16);
-    // sort-phase view (aliases the pair-phase arrays)
+    // sort-phase view (aliases the pair-phase arrays); ekl holds {key, id} by
+    // bucket position, so one 64-bit access moves an entry and one 64-bit
+    // compare orders two entries by (key, id)
     uint32_t* stg = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* ekey = stg + CAPL;
-    uint32_t* el = ekey + CAPL;
-    uint32_t* bcnt = el + CAPL;
+    uint2* ekl = reinterpret_cast<uint2*>(stg + CAPL);
+    uint32_t* bcnt = stg + 3 * CAPL;
 
     __shared__ uint32_t s_scan[NW + 1];
     __shared__ T s_redacc[NW * 8];
@@ -459,14 +471,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     __shared__ T s_par[16];
     __shared__ uint4 s_item[2];
     __shared__ typename MaxBits<T>::U s_vmax;         // largest squared speed (bit pattern)                     // current / next work item {j, N_j, I_j, valid}
-    __shared__ __align__(16) double s_cp[12];       // cell parameters: dt_factor, lnlam, inv_vol, -, mom[0..7]
+    __shared__ __align__(16) double s_cp[NCP];      // the cell's scalars of this pass (CP_* of CellParamArgs)
 
     const unsigned r = Cl<C>::rank();
     const unsigned tid = threadIdx.x;
     DevState* ds = a.ds;
     const uint32_t list_n = ds->class_n[a.cls];
     const uint32_t step = ds->step;
-    const double dt = ds->dt;
     const bool do_coul = (a.flags & F_COULOMB) != 0u;
     const bool do_neut = (a.flags & F_NEUTRAL) != 0u;
     const bool do_corr = (a.flags & F_CORRECTION) != 0u;
@@ -499,13 +510,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             Cl<C>::sync();
             continue;
         }
-        if (tid == 0) {   // this cell's parameters, consumed after the gather's wait
-            cp_async<8>(&s_cp[0], a.dt_factor + j);
-            cp_async<8>(&s_cp[1], a.lnlam + j);
-            cp_async<8>(&s_cp[2], a.inv_vol + j);
-            const double* m = a.mom + (size_t)j * NMOM;
+        if (tid == 0) {   // this cell's scalars, consumed after the gather's wait
+            const double* cpj = a.cpar + (size_t)j * NCP;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cp_async<16>(&s_cp[4 + 2 * q], m + 2 * q);
+            for (int q = 0; q < NCP / 2; ++q) cp_async<16>(&s_cp[2 * q], cpj + 2 * q);
         }
         const uint32_t nb = n_buckets(n);
         const uint32_t hb = split_begin(r, n, C), nh = split_begin(r + 1, n, C) - hb;
@@ -566,10 +574,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             }
             uint32_t tot;
             uint32_t ex = block_excl_scan<NT>(sum, s_scan, &tot);
-            if (tid == 0) s_misc[1] = tot;
-            Cl<C>::sync();
             uint32_t base = 0u;
-            for (unsigned q = 0; q < r; ++q) base += *Cl<C>::at(&s_misc[1], q);
+            if constexpr (C > 1) {
+                if (tid == 0) s_misc[1] = tot;
+                Cl<C>::sync();
+                for (unsigned q = 0; q < r; ++q) base += *Cl<C>::at(&s_misc[1], q);
+            }
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 const uint32_t bi = tid * PER + i;
@@ -594,8 +604,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     uint32_t p0;
                     const uint32_t po = PB.locate(gpos, p0);
                     const uint32_t lp = gpos - p0;
-                    *Cl<C>::at(ekey + lp, po) = stg[k];
-                    *Cl<C>::at(el + lp, po) = hl[i];
+                    *Cl<C>::at(ekl + lp, po) = make_uint2(stg[k], hl[i]);
                 } else {
                     flag_error(ds, ERR_INDEX);
                 }
@@ -607,12 +616,22 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         pc.mark(3);
         // ---- 1e. each home particle ranks itself inside its bucket: its final
         // pairing-order position is the bucket start plus the number of entries
-        // of the bucket ordered before (key, id)
+        // of the bucket ordered before (key, id).  With one bucket per particle
+        // on average almost every bucket holds at most four entries: those are
+        // loaded and compared together (independent loads, no divergent walk),
+        // and only the rare larger buckets continue serially.
+        auto entry = [&](uint32_t t) -> unsigned long long {
+            uint32_t t0;
+            const uint32_t o = PB.locate(t, t0);
+            const uint2 e = *Cl<C>::at(ekl + (t - t0), o);
+            return ((unsigned long long)e.x << 32) | e.y;
+        };
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
             if (k < nh) {
                 const uint32_t key = stg[k], l = hl[i];
+                const unsigned long long me = ((unsigned long long)key << 32) | l;
                 const uint32_t b = __umulhi(key, nb);
                 uint32_t b0;
                 const uint32_t ro = BB.locate(b, b0);
@@ -620,12 +639,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const uint32_t bs = bc[0], be = bc[1];
                 uint32_t rank = 0u;
                 if (bs <= be && be <= n) {
-                    for (uint32_t t = bs; t < be; ++t) {
-                        uint32_t t0;
-                        const uint32_t o = PB.locate(t, t0);
-                        const uint32_t kk = *Cl<C>::at(ekey + (t - t0), o);
-                        if (kk == key) rank += *Cl<C>::at(el + (t - t0), o) < l ? 1u : 0u;
-                        else rank += kk < key ? 1u : 0u;
+                    if (be - bs > 1u) {   // a bucket of one entry holds only this particle
+#pragma unroll
+                        for (uint32_t u = 0; u < 4u; ++u) {
+                            if (bs + u < be) rank += entry(bs + u) < me ? 1u : 0u;
+                        }
+                        for (uint32_t t = bs + 4u; t < be; ++t) rank += entry(t) < me ? 1u : 0u;
                     }
                 } else {
                     flag_error(ds, ERR_INDEX);
@@ -676,6 +695,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             }
             if (tid == 0) cp_async_wait_all();
         }
+        // pairing positions of the home particles, two per register, for the write-back
+        uint32_t hq[ITEMS / 2];
+#pragma unroll
+        for (int i = 0; i < ITEMS / 2; ++i) hq[i] = (hp[2 * i] & 0xFFFFu) | (hp[2 * i + 1] << 16);
         Cl<C>::sync();
 
         pc.mark(6);
@@ -697,39 +720,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // squared speed after S1 is tracked for the null-collision bound.
         T vmax2 = T(0);
         if (do_coul && n >= 2u) {
-            if (tid == 0) {   // per-cell scalars in double, once per CTA
-                const double dtj = dt * s_cp[0];
-                double lnl = s_cp[1];
-                if (a.flags & F_LNL_NRL) {
-                    const double* m = s_cp + 4;
-                    const double N = m[0];
-                    lnl = 2.0;
-                    if (N >= 2.0) {
-                        const double mx = m[2] / N, my = m[3] / N, mz = m[4] / N;
-                        const double msq = (m[5] + m[6] + m[7]) / N;
-                        const double TeV = (msq - (mx * mx + my * my + mz * mz)) / (3.0 * a.e_over_m);
-                        const double nm3 = a.weight * (double)n * s_cp[2];
-                        if (TeV > 0.0 && nm3 > 0.0) {
-                            const double lt = log(TeV);
-                            const double v = 23.5 - log(sqrt(nm3 * 1e-6) * pow(TeV, -1.25)) -
-                                             sqrt(1e-5 + (lt - 2.0) * (lt - 2.0) / 16.0);
-                            lnl = v < 2.0 ? 2.0 : v;
-                        }
-                    }
-                }
-                s_par[0] = (T)(a.coef0 * (double)n * s_cp[2] * lnl * dtj);
-                // centring shift for the restoration sums: the cell's mean velocity
-                // at the end of the previous pass (no CTA modifies it in this pass)
-                s_par[1] = s_par[2] = s_par[3] = T(0);
-                if (do_corr) {
-                    const double* m = s_cp + 4;
-                    if (m[0] > 0.0) {
-                        s_par[1] = (T)(m[2] / m[0]); s_par[2] = (T)(m[3] / m[0]); s_par[3] = (T)(m[4] / m[0]);
-                    }
-                }
-            }
-            __syncthreads();
-            const T A = s_par[0], cx = s_par[1], cy = s_par[2], cz = s_par[3];
+            // the cell's scalars in the working precision (A with lnL and dt, and the
+            // restoration's state before S1, formed at the start of the pass from the
+            // moments the previous pass left; K0 < 0 asks for the sums before S1 to be
+            // formed here instead)
+            const T A = cell_scalar<T>(s_cp, 0), cx = cell_scalar<T>(s_cp, 2), cy = cell_scalar<T>(s_cp, 3),
+                    cz = cell_scalar<T>(s_cp, 4);
+            const bool pre_mom = s_cp[CP_K0] >= 0.0;  // uniform over the cluster (same scalars)
             T acc[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[k] = T(0);
@@ -737,6 +734,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const T dx = x - cx, dy = y - cy, dz = z - cz;
                 acc[o] += dx; acc[o + 1] += dy; acc[o + 2] += dz; acc[o + 3] += dx * dx + dy * dy + dz * dz;
             };
+            const bool pre = do_corr && !pre_mom;
             const uint32_t nslot = (nloc + 1u) / 2u;
             using V2 = typename Vec2<T>::type;
             for (uint32_t p = tid; p < nslot; p += NT) {
@@ -745,50 +743,55 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const V2 Y = *reinterpret_cast<const V2*>(svy + ia);
                 const V2 Z = *reinterpret_cast<const V2*>(svz + ia);
                 T ax = X.x, ay = Y.x, az = Z.x;
-                if (do_corr) presum(ax, ay, az, 0);
+                if (pre) presum(ax, ay, az, 4);
                 if (ib < nloc) {
                     T bx = X.y, by = Y.y, bz = Z.y;
                     const uint2 L2 = *reinterpret_cast<const uint2*>(sl + ia);
-                    if (do_corr) presum(bx, by, bz, 0);
+                    if (pre) presum(bx, by, bz, 4);
                     const uint4 w = draw(a.keys, L2.x < L2.y ? L2.x : L2.y, step, TAG_PAIR);
                     ta_collide<T>(ax, ay, az, bx, by, bz, A, w);
                     *reinterpret_cast<V2*>(svx + ia) = Vec2<T>::make(ax, bx);
                     *reinterpret_cast<V2*>(svy + ia) = Vec2<T>::make(ay, by);
                     *reinterpret_cast<V2*>(svz + ia) = Vec2<T>::make(az, bz);
-                    if (do_corr) presum(bx, by, bz, 4);
+                    if (do_corr) presum(bx, by, bz, 0);
                     else vmax2 = fmax(vmax2, bx * bx + by * by + bz * bz);
                 }
-                if (do_corr) presum(ax, ay, az, 4);
+                if (do_corr) presum(ax, ay, az, 0);
                 else vmax2 = fmax(vmax2, ax * ax + ay * ay + az * az);
             }
             if (do_corr) {
-                cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
-                // V = c + S1 / n and K = S2 - |S1|^2 / n, before (0..3) and after (4..7)
-                if (tid < 7u) {   // restoration scalars from the double sums, in the working precision
-                    // (they scale binary32 velocities; a binary64 evaluation would be rounded away)
-                    const T inv_n = T(1) / (T)n;
-                    T val;
-                    if (tid == 0) {
-                        const T S0 = (T)s_tot[0], S1 = (T)s_tot[1], S2 = (T)s_tot[2], S3 = (T)s_tot[3];
-                        const T S4 = (T)s_tot[4], S5 = (T)s_tot[5], S6 = (T)s_tot[6], S7 = (T)s_tot[7];
-                        const T K0 = S3 - (S0 * S0 + S1 * S1 + S2 * S2) * inv_n;
-                        const T K1 = S7 - (S4 * S4 + S5 * S5 + S6 * S6) * inv_n;
-                        val = (K1 > T(0) && K0 > T(0)) ? Math<T>::sqrt(K0 / K1) : T(1);
+                // sums after S1 (0..3) and, without usable stored moments, before it (4..7)
+                if (pre_mom) {
+                    T acc4[4] = {acc[0], acc[1], acc[2], acc[3]};
+                    cluster_sum<NT, C, 4, T>(acc4, s_redacc, s_cl, s_tot);
+                } else {
+                    cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
+                }
+                // x <- V0 + f (x - V1) = f x + (V0 - f V1), with V = c + S1 / n and
+                // K = S2 - |S1|^2 / n from the double sums (no division in double);
+                // f and the offsets in the working precision, which they scale
+                if (tid == 0) {
+                    const double inv_n = s_cp[CP_INVN];
+                    const double c[3] = {(double)cx, (double)cy, (double)cz};
+                    double K0, V0[3];
+                    if (pre_mom) {
+                        K0 = s_cp[CP_K0];
+                        for (int q = 0; q < 3; ++q) V0[q] = s_cp[CP_C + q];
                     } else {
-                        const unsigned k = tid - 1u;            // 0..5 -> V0x V0y V0z V1x V1y V1z
-                        const unsigned comp = k % 3u;
-                        const T c = comp == 0u ? cx : comp == 1u ? cy : cz;
-                        val = c + (T)s_tot[(k / 3u) * 4u + comp] * inv_n;
+                        K0 = s_tot[7] - (s_tot[4] * s_tot[4] + s_tot[5] * s_tot[5] + s_tot[6] * s_tot[6]) * inv_n;
+                        for (int q = 0; q < 3; ++q) V0[q] = c[q] + s_tot[4 + q] * inv_n;
                     }
-                    s_par[4 + tid] = val;
+                    const double K1 = s_tot[3] - (s_tot[0] * s_tot[0] + s_tot[1] * s_tot[1] + s_tot[2] * s_tot[2]) * inv_n;
+                    const T f = (K1 > 0.0 && K0 > 0.0) ? Math<T>::sqrt((T)K0 / (T)K1) : T(1);
+                    s_par[4] = f;
+                    for (int q = 0; q < 3; ++q) s_par[5 + q] = (T)V0[q] - f * (T)(c[q] + s_tot[q] * inv_n);
                 }
                 __syncthreads();
-                const T ft = s_par[4], V0x = s_par[5], V0y = s_par[6], V0z = s_par[7], V1x = s_par[8],
-                        V1y = s_par[9], V1z = s_par[10];
+                const T ft = s_par[4], ox = s_par[5], oy = s_par[6], oz = s_par[7];
                 for (uint32_t q = tid; q < nloc; q += NT) {
-                    const T x = V0x + ft * (svx[q] - V1x);
-                    const T y = V0y + ft * (svy[q] - V1y);
-                    const T z = V0z + ft * (svz[q] - V1z);
+                    const T x = ft * svx[q] + ox;
+                    const T y = ft * svy[q] + oy;
+                    const T z = ft * svz[q] + oz;
                     svx[q] = x; svy[q] = y; svz[q] = z;
                     vmax2 = fmax(vmax2, x * x + y * y + z * z);
                 }
@@ -811,9 +814,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         if (do_neut) {
             T numax, pnull;
             uint32_t hmin;
+            const T dtj = cell_scalar<T>(s_cp, 1);
             auto bound = [&](T md, T& nmx, T& pn, uint32_t& h) {   // null-collision bound of the cell
                 nmx = a.c_nsig_tot * Math<T>::sqrt(md);
-                pn = -Math<T>::expm1(-nmx * s_par[13]);
+                pn = -Math<T>::expm1(-nmx * dtj);
                 h = cand_threshold<T>(pn);
             };
             if constexpr (C == 1) {
@@ -823,7 +827,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
                 if ((tid & 31u) == 0u) atomicMax(&s_vmax, MaxBits<T>::to(v));
-                if (tid == 0) s_par[13] = (T)(dt * s_cp[0]);
                 __syncthreads();
                 const T md = MaxBits<T>::from(s_vmax);
                 if constexpr (sizeof(T) == 4) {
@@ -835,10 +838,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 }
             } else {
                 const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl);
-                if (tid == 0) {
-                    s_par[13] = (T)(dt * s_cp[0]);
-                    bound(md, s_par[11], s_par[12], s_misc[0]);
-                }
+                if (tid == 0) bound(md, s_par[11], s_par[12], s_misc[0]);
                 __syncthreads();
                 numax = s_par[11]; pnull = s_par[12]; hmin = s_misc[0];
             }
@@ -985,15 +985,18 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             prefetch_l2(a.vy + next_l0, (size_t)cnt * sizeof(T));
             prefetch_l2(a.vz + next_l0, (size_t)cnt * sizeof(T));
         }
-        // ---- 6. write velocities back through the id list (coalesced)
+        // ---- 6. write velocities back through the id list (coalesced); the ids
+        // are read back from shared memory next to the velocities, so that they
+        // need not stay in registers through the collision phases
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
             if (k < nh) {
-                const uint32_t pos = hp[i] & 0xFFFFu, l = hl[i];
+                const uint32_t pos = (hq[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
                 uint32_t p0;
                 const uint32_t o = PB.locate(pos, p0);
                 const uint32_t lp = pos - p0;
+                const uint32_t l = *Cl<C>::at(sl + lp, o);
                 a.vx[l] = *Cl<C>::at(svx + lp, o);
                 a.vy[l] = *Cl<C>::at(svy + lp, o);
                 a.vz[l] = *Cl<C>::at(svz + lp, o);

@@ -34,9 +34,65 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
 // lane, 16-byte loads).  When they all belong to one cell -- the usual case for
 // cell-grouped storage -- one cursor atomic serves the 128 and the ids are
 // written with 16-byte stores; otherwise one atomic per warp and cell.
-static __global__ void k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
-                                 uint32_t* __restrict__ perm, const DevState* __restrict__ ds)
+// The per-cell scalars of a pass (CellParamArgs), from the cell's count, its
+// inputs and the moments left by the previous pass:
+//   * the Takizuka-Abe coefficient A = q^4 n_j lnL dt_j / (8 pi eps0^2 mu^2),
+//     n_j = w N_j / V_j, with lnL constant or by the NRL electron-electron formula
+//     from the cell's temperature and density (clamped below at 2);
+//   * for the momentum/energy restoration, the cell's mean velocity V0 and its
+//     summed squared peculiar speed K0 = sum |v|^2 - |sum v|^2 / N before the
+//     collisions.  The stored moments are sums over exactly the velocities the
+//     pass starts from when their count equals N_j; otherwise (an append rolled
+//     back by a capacity error) K0 = -1 asks the pass to form the sums itself.
+__device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
 {
+    const double* m = cp.mom + (size_t)j * NMOM;
+    const uint32_t n = cp.counts[j];
+    double* o = cp.cpar + (size_t)j * NCP;
+    const double dtj = dt * cp.dt_factor[j];
+    double lnl = cp.lnlam[j];
+    if (cp.lnl_nrl) {
+        const double N = m[0];
+        lnl = 2.0;
+        if (N >= 2.0) {
+            const double mx = m[2] / N, my = m[3] / N, mz = m[4] / N;
+            const double msq = (m[5] + m[6] + m[7]) / N;
+            const double TeV = (msq - (mx * mx + my * my + mz * mz)) / (3.0 * cp.e_over_m);
+            const double nm3 = cp.weight * (double)n * cp.inv_vol[j];
+            if (TeV > 0.0 && nm3 > 0.0) {
+                const double lt = log(TeV);
+                const double v = 23.5 - log(sqrt(nm3 * 1e-6) * pow(TeV, -1.25)) -
+                                 sqrt(1e-5 + (lt - 2.0) * (lt - 2.0) / 16.0);
+                lnl = v < 2.0 ? 2.0 : v;
+            }
+        }
+    }
+    o[CP_A] = cp.coef0 * (double)n * cp.inv_vol[j] * lnl * dtj;
+    o[CP_DT] = dtj;
+    o[CP_INVN] = n > 0u ? 1.0 / (double)n : 0.0;
+    o[CP_LNL] = lnl;
+    double K0 = -1.0;
+    for (int q = 0; q < 3; ++q) o[CP_C + q] = m[0] > 0.0 ? m[2 + q] / m[0] : 0.0;
+    if (n > 0u && m[0] == (double)n) {
+        K0 = (m[5] + m[6] + m[7]) - (m[2] * m[2] + m[3] * m[3] + m[4] * m[4]) / m[0];
+        K0 = K0 > 0.0 ? K0 : 0.0;
+    }
+    o[CP_K0] = K0;
+    float* f = reinterpret_cast<float*>(o + CP_F32);
+    f[0] = (float)o[CP_A];
+    f[1] = (float)dtj;
+    for (int q = 0; q < 3; ++q) f[2 + q] = (float)o[CP_C + q];
+    f[5] = 0.0f;
+}
+
+static __global__ void k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
+                                 uint32_t* __restrict__ perm, const DevState* __restrict__ ds, CellParamArgs cp)
+{
+    if (cp.cpar) {                                   // this pass's per-cell scalars, one thread per cell
+        const double dt = ds->dt;
+        for (int32_t j = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); j < M; j += (int32_t)(gridDim.x * blockDim.x))
+            cell_params(cp, j, dt);
+    }
     if (ds->grouping_valid) return;                  // cached grouping: perm is current
     const unsigned long long n = ds->n;
     const unsigned lane = threadIdx.x & 31u;
@@ -288,9 +344,10 @@ cudaError_t launch_hist(const int32_t* cell, uint32_t* counts, int32_t M, DevSta
 }
 
 cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uint32_t* perm, const DevState* ds,
-                           int grid, cudaStream_t s)
+                           int grid, cudaStream_t s, const CellParamArgs* cp)
 {
-    k_scatter<<<grid, 256, 0, s>>>(cell, M, cursor, perm, ds);
+    CellParamArgs none = {};
+    k_scatter<<<grid, 256, 0, s>>>(cell, M, cursor, perm, ds, cp ? *cp : none);
     return cudaGetLastError();
 }
 

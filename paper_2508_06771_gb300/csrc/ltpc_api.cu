@@ -31,7 +31,7 @@ struct Layout {
     size_t vx, vy, vz, cell, x;
     // work offsets
     size_t perm, counts, cell_start, cs_prev, cursor, ion_count, ion_off, stage_l, stage_vx, stage_vy,
-        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, lists, ds;
+        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, lists, ds;
 };
 
 bool compute_layout(const ltpc_config* c, Layout* L)
@@ -65,6 +65,7 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->inv_vol = take(M * 8);
     L->dt_factor = take(M * 8);
     L->lnlam = take(M * 8);
+    L->cpar = take(M * NCP * 8);
     L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
     L->work = o;
@@ -154,9 +155,7 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.perm = ctx->w<uint32_t>(L.perm);
     a.counts = ctx->w<uint32_t>(L.counts);
     a.cell_start = ctx->w<uint32_t>(L.cell_start);
-    a.inv_vol = ctx->w<double>(L.inv_vol);
-    a.dt_factor = ctx->w<double>(L.dt_factor);
-    a.lnlam = ctx->w<double>(L.lnlam);
+    a.cpar = ctx->w<double>(L.cpar);
     a.mom = ctx->w<double>(L.mom);
     a.hist = ctx->w<uint32_t>(L.hist);
     a.ion_count = ctx->w<uint32_t>(L.ion_count);
@@ -200,8 +199,19 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
     int ei = 0;
     auto mark = [&]() -> cudaError_t { return ev ? cudaEventRecord(ev[ei++], s) : cudaSuccess; };
     CK(mark());
+    CellParamArgs cp = {};
+    cp.counts = ctx->w<uint32_t>(L.counts);
+    cp.mom = ctx->w<double>(L.mom);
+    cp.inv_vol = ctx->w<double>(L.inv_vol);
+    cp.dt_factor = ctx->w<double>(L.dt_factor);
+    cp.lnlam = ctx->w<double>(L.lnlam);
+    cp.cpar = ctx->w<double>(L.cpar);
+    cp.coef0 = ctx->coef0;
+    cp.weight = ctx->cfg.weight;
+    cp.e_over_m = ctx->cfg.charge / ctx->cfg.mass;
+    cp.lnl_nrl = ctx->cfg.lnlambda_mode == LTPC_LNL_NRL ? 1 : 0;
     CK(launch_scatter(ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
-                      grid_stream, s));
+                      grid_stream, s, &cp));
     CK(mark());
     CellArgs<T> a = make_args<T>(ctx, flags);
     a.order_out = order_out;

@@ -43,6 +43,31 @@ struct DevState {
     unsigned int grouping_valid;      // 1: perm still groups the particles (no load, no append since)
 };
 
+// Per-cell scalars of one pass, formed by a grid-wide loop at the start of
+// the pass (in the scatter kernel) from the cell's inputs and the moments of
+// the previous pass, so that the cell kernel reads them instead of deriving
+// them on one thread while its CTA waits.  Twelve doubles per cell.
+enum : int {
+    CP_A = 0,        // Takizuka-Abe coefficient: <delta^2> = A / |u|^3 (includes lnL and dt of the cell)
+    CP_DT = 1,       // dt of the cell
+    CP_K0 = 2,       // sum of squared peculiar speeds of the cell (restoration), -1: recompute in the pass
+    CP_C = 3,        // 3..5: mean velocity of the cell (restoration target and centring shift)
+    CP_INVN = 6,     // 1 / N_j
+    CP_LNL = 7,      // Coulomb logarithm used
+    CP_F32 = 8,      // 8..10: A, dt and the mean velocity rounded to binary32 (five floats)
+    NCP = 12
+};
+struct CellParamArgs {
+    const uint32_t* counts;      // N_j of this pass
+    const double* mom;           // moments of the previous pass (or of the load)
+    const double* inv_vol;
+    const double* dt_factor;
+    const double* lnlam;
+    double* cpar;                // [M][NCP] out; nullptr: not formed
+    double coef0, weight, e_over_m;
+    int lnl_nrl;                 // 1: Coulomb logarithm by the NRL e-e formula
+};
+
 // Arguments of the cell kernel (one cluster per cell).
 template <class T>
 struct CellArgs {
@@ -51,9 +76,7 @@ struct CellArgs {
     const uint32_t* perm;        // particle ids grouped by cell (CCS3 output)
     const uint32_t* counts;      // N_j
     const uint32_t* cell_start;  // I_j
-    const double* inv_vol;       // 1 / V_j
-    const double* dt_factor;     // per-cell multiplier of dt
-    const double* lnlam;         // constant Coulomb logarithm per cell
+    const double* cpar;          // [M][NCP] per-cell scalars of this pass
     double* mom;                 // [M][NMOM]
     uint32_t* hist;              // [M][NBIN]
     uint32_t* ion_count;         // [M] secondaries staged by this pass

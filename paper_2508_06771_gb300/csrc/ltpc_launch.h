@@ -51,7 +51,7 @@ int class_tables(int precision, const ClassTable** out);
 // Host-side launchers of the grouping / bookkeeping kernels (k_group.cu).
 cudaError_t launch_hist(const int32_t* cell, uint32_t* counts, int32_t M, DevState* ds, int grid, cudaStream_t s);
 cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uint32_t* perm, const DevState* ds, int grid,
-                           cudaStream_t s);
+                           cudaStream_t s, const CellParamArgs* cp = nullptr);
 cudaError_t launch_regroup(int32_t M, uint32_t* counts, uint32_t* cell_start, uint32_t* cs_prev, uint32_t* cursor,
                            uint32_t* ion_count, uint32_t* ion_off, const RegroupLists& lists,
                            unsigned long long capacity, int append, int advance_step, DevState* ds, cudaStream_t s);

@@ -104,6 +104,17 @@ template <> __device__ __forceinline__ float unif<float>(uint32_t w)
     return unif24(w >> 8);
 }
 
+// Uniform variate for an angle, on [0, 1): only its distribution matters, not
+// that it avoids 0.  binary64 keeps unif (the 1e-12 parity bar needs the same
+// value as the FP64 reference); binary32 takes the top 23 bits as the mantissa
+// of a float in [1, 2) and subtracts 1 (exact): three instructions instead of
+// the eight of unif<float>, and within 2^-23 of it.
+template <class T> __device__ __forceinline__ T unif_angle(uint32_t w) { return unif<T>(w); }
+template <> __device__ __forceinline__ float unif_angle<float>(uint32_t w)
+{
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 1.0f;
+}
+
 // Range of unif(w) over all w sharing the top 16 bits `hi` (used to decide
 // the null-collision candidate test without redrawing the stream).
 template <class T> __device__ __forceinline__ void unif_hi16_range(uint32_t hi, T& lo, T& up);
