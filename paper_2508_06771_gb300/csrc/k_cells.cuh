@@ -108,16 +108,19 @@ template <> struct Math<double> {
     }
 };
 
-// Takizuka-Abe binary collision of an equal-mass pair (a, b); A is the cell
-// coefficient so that <delta^2> = A / |u|^3; w holds the pair's three uniforms
-// (Box-Muller radius and angle for delta, then the azimuth phi).
+// Takizuka-Abe binary collision of an equal-mass pair (a, b): the change
+// Delta u of the relative velocity (zero when u = 0); the caller applies
+// v_a += Delta u / 2, v_b -= Delta u / 2.  A is the cell coefficient so that
+// <delta^2> = A / |u|^3; w holds the pair's three uniforms (Box-Muller radius
+// and angle for delta, then the azimuth phi).
 template <class T>
-__device__ __forceinline__ void ta_collide(T& ax, T& ay, T& az, T& bx, T& by, T& bz, T A, uint4 w)
+__device__ __forceinline__ void ta_delta(T ax, T ay, T az, T bx, T by, T bz, T A, uint4 w, T& dux, T& duy, T& duz)
 {
     using M = Math<T>;
     const T ux = ax - bx, uy = ay - by, uz = az - bz;
     const T up2 = ux * ux + uy * uy;
     const T usq = up2 + uz * uz;
+    dux = duy = duz = T(0);
     if (usq == T(0)) return;
     const T u = M::sqrt(usq);
     const T iu = M::rcp(u);
@@ -132,7 +135,6 @@ __device__ __forceinline__ void ta_collide(T& ax, T& ay, T& az, T& bx, T& by, T&
     const T rr = M::rcp(T(1) + t * t);
     const T sin_t = T(2) * t * rr;
     const T omc_t = small ? T(2) * t * t * rr : T(2) * rr;
-    T dux, duy, duz;
     if (up2 > T(0)) {
         const T uperp = M::sqrt(up2);
         const T ip = M::rcp(uperp);
@@ -146,9 +148,6 @@ __device__ __forceinline__ void ta_collide(T& ax, T& ay, T& az, T& bx, T& by, T&
         duy = u * sin_t * sph;
         duz = -uz * omc_t;
     }
-    const T h = T(0.5);
-    ax += h * dux; ay += h * duy; az += h * duz;
-    bx -= h * dux; by -= h * duy; bz -= h * duz;
 }
 
 // Isotropic unit vector from two uniforms: cos(theta) = 1 - 2 U_a, phi = 2 pi U_b.
@@ -185,9 +184,39 @@ template <> struct Vec2<double> {
     static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
 };
 
+// Exclusive prefix sum of one value per thread over the CTA, and the total.
+// One barrier: every warp scans the warps' totals itself.  Callers pass a
+// barrier before s_scan is written again (the next call).
+// Two values of the working precision processed together: binary32 maps onto
+// the packed FADD2/FMUL2/FFMA2 instructions (one issue for both lanes, each
+// lane rounded exactly as its scalar form); binary64 stays scalar.
+template <class T> struct Pk;
+// Accumulators: sum (X) and sum (X^2) of both lanes into s; binary32 keeps one
+// partial per lane, binary64 folds both into the first lane (no registers for
+// a second lane, which would bring no speed).
+template <> struct Pk<float> {
+    using V = float2;
+    static __device__ __forceinline__ V make(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ void acc(V& s, V x) { s = __fadd2_rn(s, x); }
+    static __device__ __forceinline__ void acc_sq(V& s, V x) { s = __ffma2_rn(x, x, s); }
+};
+template <> struct Pk<double> {
+    using V = double2;
+    static __device__ __forceinline__ V make(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+    static __device__ __forceinline__ void acc(V& s, V x) { s.x += x.x; s.x += x.y; }
+    static __device__ __forceinline__ void acc_sq(V& s, V x) { s.x = ::fma(x.x, x.x, s.x); s.x = ::fma(x.y, x.y, s.x); }
+};
+
 template <int NT>
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_scan, uint32_t* total)
 {
+    constexpr int NW = NT / 32;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -197,21 +226,15 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_scan
     }
     if (lane == 31u) s_scan[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t wv = lane < NT / 32 ? s_scan[lane] : 0u;
-        uint32_t z = wv;
+    const uint32_t wv = lane < (unsigned)NW ? s_scan[lane] : 0u;
+    uint32_t z = wv;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
-            if (lane >= (unsigned)o) z += y;
-        }
-        if (lane < NT / 32) s_scan[lane] = z - wv;
-        if (lane == NT / 32 - 1) s_scan[NT / 32] = z;
+    for (int o = 1; o < NW; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+        if (lane >= (unsigned)o) z += y;
     }
-    __syncthreads();
-    const uint32_t res = s_scan[warp] + x - v;
-    *total = s_scan[NT / 32];
-    return res;   // callers pass a barrier before s_scan is written again
+    *total = __shfl_sync(0xFFFFFFFFu, z, NW - 1);
+    return __shfl_sync(0xFFFFFFFFu, z - wv, warp) + x - v;
 }
 
 constexpr uint32_t LISTCAP = 512;    // positions handled per round of a masked pass
@@ -238,7 +261,8 @@ __device__ __forceinline__ void for_each_masked(uint32_t* mask, uint32_t nw, uin
         __syncthreads();
         const uint32_t nl = total - base < LISTCAP ? total - base : LISTCAP;
         for (uint32_t i = tid; i < nl; i += NT) f(list[i]);
-        __syncthreads();
+        if (base + LISTCAP < total) __syncthreads();   // the list is refilled; after the
+                                                       // last round the caller's next barrier serves
     }
     if (tid < nw) mask[tid] = 0u;
 }
@@ -248,7 +272,8 @@ __device__ __forceinline__ void for_each_masked(uint32_t* mask, uint32_t nw, uin
 // partial), then the warps' partials in double by one warp -- lane l takes
 // quantity l % NQ and every (32 / NQ)-th warp partial, summed as a tree, and
 // the lanes of a quantity are combined by xor shuffles -- and the CTAs in rank
-// order in double.  Deterministic for a given block shape.
+// order in double.  Deterministic for a given block shape.  With C = 1 only
+// warp 0 may read `out` afterwards (its lanes wrote it); with C > 1 every thread.
 template <int NT, int C, int NQ, class A>
 __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, double* out)
 {
@@ -283,8 +308,16 @@ __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, 
         double t = x[0];
 #pragma unroll
         for (int o = NQ; o < 32; o <<= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-        if (lane < (unsigned)NQ) s_cl[lane] = t;
+        if constexpr (C == 1) {
+            // a single CTA: warp 0 holds the totals; its callers read them from
+            // warp 0 only, so no further barrier
+            if (lane < (unsigned)NQ) out[lane] = 0.0 + t;
+            __syncwarp();
+        } else {
+            if (lane < (unsigned)NQ) s_cl[lane] = t;
+        }
     }
+    if constexpr (C == 1) return;
     Cl<C>::sync();
     if (threadIdx.x < (unsigned)NQ) {
         double acc = 0.0;
@@ -727,40 +760,57 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const T A = cell_scalar<T>(s_cp, 0), cx = cell_scalar<T>(s_cp, 2), cy = cell_scalar<T>(s_cp, 3),
                     cz = cell_scalar<T>(s_cp, 4);
             const bool pre_mom = s_cp[CP_K0] >= 0.0;  // uniform over the cluster (same scalars)
-            T acc[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = T(0);
-            auto presum = [&](T x, T y, T z, int o) {
-                const T dx = x - cx, dy = y - cy, dz = z - cz;
-                acc[o] += dx; acc[o + 1] += dy; acc[o + 2] += dz; acc[o + 3] += dx * dx + dy * dy + dz * dz;
+            // Pair slot p holds positions 2p and 2p+1, so the pair's two particles sit
+            // in the two lanes of one packed value: the update v_a += Du/2, v_b -= Du/2
+            // and the sums are packed operations.  The restoration and the moments
+            // below walk the same slots, so each thread rereads what it wrote.
+            using P = Pk<T>;
+            using V2 = typename P::V;
+            const V2 C2x = P::make(-cx, -cx), C2y = P::make(-cy, -cy), C2z = P::make(-cz, -cz);
+            V2 sx = P::make(T(0), T(0)), sy = sx, sz = sx, ss = sx;      // after S1 (centred)
+            V2 bx0 = sx, by0 = sx, bz0 = sx, bs0 = sx;                    // before S1, if needed
+            auto psum = [&](V2 X, V2 Y, V2 Z, V2& ax_, V2& ay_, V2& az_, V2& as_) {
+                const V2 dx = P::add(X, C2x), dy = P::add(Y, C2y), dz = P::add(Z, C2z);
+                P::acc(ax_, dx); P::acc(ay_, dy); P::acc(az_, dz);
+                P::acc(as_, P::fma(dz, dz, P::fma(dy, dy, P::mul(dx, dx))));
             };
             const bool pre = do_corr && !pre_mom;
             const uint32_t nslot = (nloc + 1u) / 2u;
-            using V2 = typename Vec2<T>::type;
+            const V2 H = P::make(T(0.5), T(-0.5));
             for (uint32_t p = tid; p < nslot; p += NT) {
                 const uint32_t ia = 2u * p, ib = ia + 1u;   // pair slots are even-aligned: one vector access each
-                const V2 X = *reinterpret_cast<const V2*>(svx + ia);
-                const V2 Y = *reinterpret_cast<const V2*>(svy + ia);
-                const V2 Z = *reinterpret_cast<const V2*>(svz + ia);
-                T ax = X.x, ay = Y.x, az = Z.x;
-                if (pre) presum(ax, ay, az, 4);
+                V2 X = *reinterpret_cast<const V2*>(svx + ia);
+                V2 Y = *reinterpret_cast<const V2*>(svy + ia);
+                V2 Z = *reinterpret_cast<const V2*>(svz + ia);
                 if (ib < nloc) {
-                    T bx = X.y, by = Y.y, bz = Z.y;
                     const uint2 L2 = *reinterpret_cast<const uint2*>(sl + ia);
-                    if (pre) presum(bx, by, bz, 4);
+                    if (pre) psum(X, Y, Z, bx0, by0, bz0, bs0);
                     const uint4 w = draw(a.keys, L2.x < L2.y ? L2.x : L2.y, step, TAG_PAIR);
-                    ta_collide<T>(ax, ay, az, bx, by, bz, A, w);
-                    *reinterpret_cast<V2*>(svx + ia) = Vec2<T>::make(ax, bx);
-                    *reinterpret_cast<V2*>(svy + ia) = Vec2<T>::make(ay, by);
-                    *reinterpret_cast<V2*>(svz + ia) = Vec2<T>::make(az, bz);
-                    if (do_corr) presum(bx, by, bz, 0);
-                    else vmax2 = fmax(vmax2, bx * bx + by * by + bz * bz);
+                    T dux, duy, duz;
+                    ta_delta<T>(X.x, Y.x, Z.x, X.y, Y.y, Z.y, A, w, dux, duy, duz);
+                    X = P::fma(H, P::make(dux, dux), X);
+                    Y = P::fma(H, P::make(duy, duy), Y);
+                    Z = P::fma(H, P::make(duz, duz), Z);
+                    *reinterpret_cast<V2*>(svx + ia) = X;
+                    *reinterpret_cast<V2*>(svy + ia) = Y;
+                    *reinterpret_cast<V2*>(svz + ia) = Z;
+                    if (do_corr) {
+                        psum(X, Y, Z, sx, sy, sz, ss);
+                    } else {
+                        const V2 q2 = P::fma(Z, Z, P::fma(Y, Y, P::mul(X, X)));
+                        vmax2 = fmax(vmax2, fmax(q2.x, q2.y));
+                    }
+                } else {                                      // the odd one out: unchanged
+                    const V2 X1 = P::make(X.x, cx), Y1 = P::make(Y.x, cy), Z1 = P::make(Z.x, cz);
+                    if (pre) psum(X1, Y1, Z1, bx0, by0, bz0, bs0);
+                    if (do_corr) psum(X1, Y1, Z1, sx, sy, sz, ss);
+                    else vmax2 = fmax(vmax2, X.x * X.x + Y.x * Y.x + Z.x * Z.x);
                 }
-                if (do_corr) presum(ax, ay, az, 0);
-                else vmax2 = fmax(vmax2, ax * ax + ay * ay + az * az);
             }
             if (do_corr) {
                 // sums after S1 (0..3) and, without usable stored moments, before it (4..7)
+                T acc[8] = {sx.x + sx.y, sy.x + sy.y, sz.x + sz.y, ss.x + ss.y,
+                            bx0.x + bx0.y, by0.x + by0.y, bz0.x + bz0.y, bs0.x + bs0.y};
                 if (pre_mom) {
                     T acc4[4] = {acc[0], acc[1], acc[2], acc[3]};
                     cluster_sum<NT, C, 4, T>(acc4, s_redacc, s_cl, s_tot);
@@ -787,16 +837,30 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     for (int q = 0; q < 3; ++q) s_par[5 + q] = (T)V0[q] - f * (T)(c[q] + s_tot[q] * inv_n);
                 }
                 __syncthreads();
-                const T ft = s_par[4], ox = s_par[5], oy = s_par[6], oz = s_par[7];
-                for (uint32_t q = tid; q < nloc; q += NT) {
-                    const T x = ft * svx[q] + ox;
-                    const T y = ft * svy[q] + oy;
-                    const T z = ft * svz[q] + oz;
-                    svx[q] = x; svy[q] = y; svz[q] = z;
-                    vmax2 = fmax(vmax2, x * x + y * y + z * z);
+                const V2 F = P::make(s_par[4], s_par[4]);
+                const V2 OX = P::make(s_par[5], s_par[5]), OY = P::make(s_par[6], s_par[6]),
+                         OZ = P::make(s_par[7], s_par[7]);
+                for (uint32_t p = tid; p < nslot; p += NT) {
+                    const uint32_t ia = 2u * p;
+                    const V2 X = P::fma(F, *reinterpret_cast<const V2*>(svx + ia), OX);
+                    const V2 Y = P::fma(F, *reinterpret_cast<const V2*>(svy + ia), OY);
+                    const V2 Z = P::fma(F, *reinterpret_cast<const V2*>(svz + ia), OZ);
+                    const V2 q2 = P::fma(Z, Z, P::fma(Y, Y, P::mul(X, X)));
+                    if (ia + 1u < nloc) {
+                        *reinterpret_cast<V2*>(svx + ia) = X;
+                        *reinterpret_cast<V2*>(svy + ia) = Y;
+                        *reinterpret_cast<V2*>(svz + ia) = Z;
+                        vmax2 = fmax(vmax2, fmax(q2.x, q2.y));
+                    } else {
+                        svx[ia] = X.x; svy[ia] = Y.x; svz[ia] = Z.x;
+                        vmax2 = fmax(vmax2, q2.x);
+                    }
                 }
             }
-            __syncthreads();
+            // A single CTA needs no barrier here: the next reads of these positions
+            // are by the same threads (same pair slots), or the neutral step follows
+            // (its first action is a barrier).
+            if (C > 1) __syncthreads();
         } else if (do_neut) {
             for (uint32_t q = tid; q < nloc; q += NT) {
                 const T x = svx[q], y = svy[q], z = svz[q];
@@ -916,19 +980,35 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // ---- 5. ionization outcomes (C2), then the moments (S3a/S3b) of the cell
         {
             using M = Math<T>;
+            using P = Pk<T>;
+            using V2 = typename P::V;
             const T e_ion = a.c_e_ion, two_e_over_m = a.c_two_e_over_m;
-            T acc[8];
+            // per-thread sums, two lanes each (positions 2p and 2p+1 of the pair slots):
+            // v_x, v_y, v_z, v_x^2, v_y^2, v_z^2, |v|, |v| above the ionization threshold
+            V2 q[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = T(0);
+            for (int k = 0; k < 8; ++k) q[k] = P::make(T(0), T(0));
             uint32_t* hsub = s_hist + ((tid >> 5) & 3u) * NBIN;
-            auto accum = [&](T x, T y, T z) {
+            const V2 HM = P::make(half_m_over_e, half_m_over_e);
+            auto accum2 = [&](V2 X, V2 Y, V2 Z) {
+                const V2 v2 = P::fma(Z, Z, P::fma(Y, Y, P::mul(X, X)));
+                const V2 V = P::make(M::sqrt(v2.x), M::sqrt(v2.y));
+                const V2 E = P::mul(v2, HM);
+                P::acc(q[0], X); P::acc(q[1], Y); P::acc(q[2], Z);
+                P::acc_sq(q[3], X); P::acc_sq(q[4], Y); P::acc_sq(q[5], Z);
+                P::acc(q[6], V);
+                P::acc(q[7], P::make(E.x >= e_ion ? V.x : T(0), E.y >= e_ion ? V.y : T(0)));
+                atomicAdd(&hsub[M::ebin(E.x)], 1u);
+                atomicAdd(&hsub[M::ebin(E.y)], 1u);
+            };
+            auto accum = [&](T x, T y, T z) {                  // one particle, into the first lane
                 const T v2 = x * x + y * y + z * z;
                 const T v = M::sqrt(v2);
                 const T E = v2 * half_m_over_e;
-                acc[0] += x; acc[1] += y; acc[2] += z;
-                acc[3] += x * x; acc[4] += y * y; acc[5] += z * z;
-                acc[6] += v;
-                acc[7] += E >= e_ion ? v : T(0);
+                q[0].x += x; q[1].x += y; q[2].x += z;
+                q[3].x += x * x; q[4].x += y * y; q[5].x += z * z;
+                q[6].x += v;
+                q[7].x += E >= e_ion ? v : T(0);
                 atomicAdd(&hsub[M::ebin(E)], 1u);
             };
             if (do_neut && s_misc[2] > 0u) {
@@ -954,8 +1034,19 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     a.stage_vx[slot] = sx; a.stage_vy[slot] = sy; a.stage_vz[slot] = sz;
                     accum(sx, sy, sz);
                 });
+                __syncthreads();   // the primaries' new velocities before the sums below
             }
-            for (uint32_t q = tid; q < nloc; q += NT) accum(svx[q], svy[q], svz[q]);
+            for (uint32_t p = tid; 2u * p < nloc; p += NT) {
+                const uint32_t ia = 2u * p;
+                const V2 X = *reinterpret_cast<const V2*>(svx + ia);
+                const V2 Y = *reinterpret_cast<const V2*>(svy + ia);
+                const V2 Z = *reinterpret_cast<const V2*>(svz + ia);
+                if (ia + 1u < nloc) accum2(X, Y, Z);
+                else accum(X.x, Y.x, Z.x);
+            }
+            T acc[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = q[k].x + q[k].y;
             cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
             if (r == 0 && tid < (unsigned)NBIN) {
                 uint32_t h = 0u;

@@ -46,46 +46,53 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
 //     back by a capacity error) K0 = -1 asks the pass to form the sums itself.
 __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
 {
+    // One binary64 division per cell (1 / sum of counts of the stored moments);
+    // everything else is products, since binary64 runs on a narrow pipe here.
     const double* m = cp.mom + (size_t)j * NMOM;
     const uint32_t n = cp.counts[j];
     double* o = cp.cpar + (size_t)j * NCP;
     const double dtj = dt * cp.dt_factor[j];
+    const double N = m[0];
+    const double iN = N > 0.0 ? 1.0 / N : 0.0;
+    const double mean[3] = {m[2] * iN, m[3] * iN, m[4] * iN};
+    const double s2 = m[5] + m[6] + m[7];
     double lnl = cp.lnlam[j];
     if (cp.lnl_nrl) {
-        const double N = m[0];
         lnl = 2.0;
         if (N >= 2.0) {
-            const double mx = m[2] / N, my = m[3] / N, mz = m[4] / N;
-            const double msq = (m[5] + m[6] + m[7]) / N;
-            const double TeV = (msq - (mx * mx + my * my + mz * mz)) / (3.0 * cp.e_over_m);
+            const double TeV = (s2 * iN - (mean[0] * mean[0] + mean[1] * mean[1] + mean[2] * mean[2])) /
+                               (3.0 * cp.e_over_m);
             const double nm3 = cp.weight * (double)n * cp.inv_vol[j];
             if (TeV > 0.0 && nm3 > 0.0) {
+                // 23.5 - ln(n^1/2 T^-5/4) - (1e-5 + (ln T - 2)^2 / 16)^1/2, n in cm^-3, T in eV
                 const double lt = log(TeV);
-                const double v = 23.5 - log(sqrt(nm3 * 1e-6) * pow(TeV, -1.25)) -
-                                 sqrt(1e-5 + (lt - 2.0) * (lt - 2.0) / 16.0);
+                const double v = 23.5 - (0.5 * log(nm3 * 1e-6) - 1.25 * lt) -
+                                 sqrt(1e-5 + (lt - 2.0) * (lt - 2.0) * 0.0625);
                 lnl = v < 2.0 ? 2.0 : v;
             }
         }
     }
     o[CP_A] = cp.coef0 * (double)n * cp.inv_vol[j] * lnl * dtj;
     o[CP_DT] = dtj;
-    o[CP_INVN] = n > 0u ? 1.0 / (double)n : 0.0;
     o[CP_LNL] = lnl;
+    for (int q = 0; q < 3; ++q) o[CP_C + q] = mean[q];
     double K0 = -1.0;
-    for (int q = 0; q < 3; ++q) o[CP_C + q] = m[0] > 0.0 ? m[2 + q] / m[0] : 0.0;
-    if (n > 0u && m[0] == (double)n) {
-        K0 = (m[5] + m[6] + m[7]) - (m[2] * m[2] + m[3] * m[3] + m[4] * m[4]) / m[0];
+    if (n > 0u && N == (double)n) {
+        K0 = s2 - (m[2] * mean[0] + m[3] * mean[1] + m[4] * mean[2]);
         K0 = K0 > 0.0 ? K0 : 0.0;
+        o[CP_INVN] = iN;
+    } else {
+        o[CP_INVN] = n > 0u ? 1.0 / (double)n : 0.0;
     }
     o[CP_K0] = K0;
     float* f = reinterpret_cast<float*>(o + CP_F32);
     f[0] = (float)o[CP_A];
     f[1] = (float)dtj;
-    for (int q = 0; q < 3; ++q) f[2 + q] = (float)o[CP_C + q];
+    for (int q = 0; q < 3; ++q) f[2 + q] = (float)mean[q];
     f[5] = 0.0f;
 }
 
-static __global__ void k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
+static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
                                  uint32_t* __restrict__ perm, const DevState* __restrict__ ds, CellParamArgs cp)
 {
     if (cp.cpar) {                                   // this pass's per-cell scalars, one thread per cell
