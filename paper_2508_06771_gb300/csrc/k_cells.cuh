@@ -1021,7 +1021,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     const T E = (x * x + y * y + z * z) * half_m_over_e;
                     const uint4 sc = draw(a.keys, l, step, TAG_SCATTER);
                     const uint4 sd = draw(a.keys, l, step, TAG_SECONDARY);
-                    const T Ep = E - e_ion;
+                    // E was >= e_ion when the collision was decided; recomputed here it can
+                    // round one unit below, so the excess is clamped at zero (a negative
+                    // excess would give a NaN speed)
+                    const T Ep = fmax(E - e_ion, T(0));
                     const T Es = unif<T>(sc.z) * Ep;
                     const T vp = M::sqrt(two_e_over_m * (Ep - Es)), vs = M::sqrt(two_e_over_m * Es);
                     T dx, dy, dz, ex2, ey2, ez2;
