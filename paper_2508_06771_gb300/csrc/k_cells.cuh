@@ -548,7 +548,14 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
 #pragma unroll
             for (int q = 0; q < NCP / 2; ++q) cp_async<16>(&s_cp[2 * q], cpj + 2 * q);
         }
-        const uint32_t nb = n_buckets(n);
+        // Buckets of the pairing-order sort.  A single CTA uses two buckets per
+        // particle with 16-bit counters (two per word, in the space of one 32-bit
+        // counter per particle), so that most particles are alone in their bucket
+        // and take their position straight from the bucket scan; clusters use one
+        // bucket per particle with 32-bit counters spread over the CTAs.
+        constexpr bool SB = C == 1;
+        const uint32_t nb = SB ? 2u * n : n_buckets(n);
+        uint16_t* const b16 = reinterpret_cast<uint16_t*>(bcnt);
         const uint32_t hb = split_begin(r, n, C), nh = split_begin(r + 1, n, C) - hb;
         const uint32_t bb = split_begin(r, nb, C), nbl = split_begin(r + 1, nb, C) - bb;
         const uint32_t pb = pos_begin(r, n, C), pe = pos_end(r, n, C);
@@ -558,7 +565,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         BB.init_split(nb);
 
         // ---- 1a. zero this CTA's bucket counters and histogram
-        for (uint32_t i = tid; i <= nbl; i += NT) bcnt[i] = 0u;
+        for (uint32_t i = tid; i <= (SB ? n : nbl); i += NT) bcnt[i] = 0u;   // (SB: n + 1 words)
         for (uint32_t i = tid; i < 4u * NBIN; i += NT) s_hist[i] = 0u;
         for (uint32_t i = tid; i < CAPL / 32u; i += NT) s_imask[i] = 0u;
         if (tid == 0) s_vmax = 0u;
@@ -580,9 +587,15 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const uint32_t l = hl[i];
                 const uint4 rw = draw(a.keys, l, step, TAG_PARTICLE);
                 const uint32_t b = __umulhi(rw.x, nb);
-                uint32_t b0;
-                const uint32_t ro = BB.locate(b, b0);
-                const uint32_t slot = atomicAdd(Cl<C>::at(bcnt + (b - b0), ro), 1u);
+                uint32_t slot;
+                if constexpr (SB) {
+                    const uint32_t sh = (b & 1u) << 4;
+                    slot = atomicAdd(bcnt + (b >> 1), 1u << sh) >> sh;
+                } else {
+                    uint32_t b0;
+                    const uint32_t ro = BB.locate(b, b0);
+                    slot = atomicAdd(Cl<C>::at(bcnt + (b - b0), ro), 1u);
+                }
                 stg[k] = rw.x;
                 sw[k] = (uint16_t)(rw.y >> 16);
                 hp[i] = (b << 16) | (slot & 0xFFFFu);
@@ -596,7 +609,27 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
 
         pc.mark(1);
         // ---- 1c. bucket starts: local exclusive scan, then offset by lower CTAs' totals
-        {
+        if constexpr (SB) {
+            // words [0, n]: bucket 2w in the low half, 2w+1 in the high half; word n
+            // has no particles, so its low half becomes the end sentinel n
+            uint32_t cnt[PER];
+            uint32_t sum = 0u;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const uint32_t bi = tid * PER + i;
+                cnt[i] = bi <= n ? bcnt[bi] : 0u;
+                sum += (cnt[i] & 0xFFFFu) + (cnt[i] >> 16);
+            }
+            uint32_t tot;
+            uint32_t ex = block_excl_scan<NT>(sum, s_scan, &tot);
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const uint32_t bi = tid * PER + i;
+                const uint32_t lo = cnt[i] & 0xFFFFu;
+                if (bi <= n) bcnt[bi] = ex | ((ex + lo) << 16);
+                ex += lo + (cnt[i] >> 16);
+            }
+        } else {
             uint32_t cnt[PER];
             uint32_t sum = 0u;
 #pragma unroll
@@ -624,7 +657,30 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         Cl<C>::sync();
 
         pc.mark(2);
-        // ---- 1d. place (key, id) at bucket start + slot, in the position-owner CTA
+        // ---- 1d. place (key, id) at bucket start + slot, in the position-owner CTA.
+        // SB: a particle alone in its bucket has its final position already.
+        uint32_t multi = 0u;           // SB: items whose bucket holds several entries
+        if constexpr (SB) {
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t k = tid + (uint32_t)i * NT;
+                if (k < nh) {
+                    const uint32_t b = hp[i] >> 16, slot = hp[i] & 0xFFFFu;
+                    const uint32_t bs = b16[b], be = b16[b + 1];
+                    if (bs + slot < be && be <= n) {
+                        if (be - bs == 1u) {
+                            hp[i] = bs | ((uint32_t)sw[k] << 16);
+                        } else {
+                            ekl[bs + slot] = make_uint2(stg[k], hl[i]);
+                            multi |= 1u << i;
+                        }
+                    } else {
+                        flag_error(ds, ERR_INDEX);
+                        hp[i] = 0u;
+                    }
+                }
+            }
+        } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
@@ -644,6 +700,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 hp[i] = gpos;
             }
         }
+        }
         Cl<C>::sync();
 
         pc.mark(3);
@@ -659,6 +716,24 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const uint2 e = *Cl<C>::at(ekl + (t - t0), o);
             return ((unsigned long long)e.x << 32) | e.y;
         };
+        if constexpr (SB) {
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                if (multi & (1u << i)) {
+                    const uint32_t k = tid + (uint32_t)i * NT;
+                    const unsigned long long me = ((unsigned long long)stg[k] << 32) | hl[i];
+                    const uint32_t b = hp[i] >> 16;
+                    const uint32_t bs = b16[b], be = b16[b + 1];   // checked in 1d: bs < be <= n
+                    uint32_t rank = 0u;
+#pragma unroll
+                    for (uint32_t u = 0; u < 4u; ++u) {
+                        if (bs + u < be) rank += entry(bs + u) < me ? 1u : 0u;
+                    }
+                    for (uint32_t t = bs + 4u; t < be; ++t) rank += entry(t) < me ? 1u : 0u;
+                    hp[i] = (bs + rank) | ((uint32_t)sw[k] << 16);
+                }
+            }
+        } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
@@ -686,6 +761,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 if (pos >= n) { flag_error(ds, ERR_INDEX); pos = 0u; }
                 hp[i] = pos | ((uint32_t)sw[k] << 16);
             }
+        }
         }
         Cl<C>::sync();
 
