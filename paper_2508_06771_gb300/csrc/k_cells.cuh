@@ -428,7 +428,8 @@ struct Bounds {
 };
 
 // Scalar k of the cell's record in the working precision: 0 = A, 1 = dt,
-// 2..4 = mean velocity (binary32 copies made with the record; binary64 as is).
+// 2..4 = mean velocity, 5 = K0, 6 = 1 / N_j (binary32 copies made with the
+// record; binary64 as is).
 template <class T> __device__ __forceinline__ T cell_scalar(const double* cp, int k);
 template <> __device__ __forceinline__ float cell_scalar<float>(const double* cp, int k)
 {
@@ -436,7 +437,7 @@ template <> __device__ __forceinline__ float cell_scalar<float>(const double* cp
 }
 template <> __device__ __forceinline__ double cell_scalar<double>(const double* cp, int k)
 {
-    return cp[k == 0 ? CP_A : k == 1 ? CP_DT : CP_C + (k - 2)];
+    return cp[k == 0 ? CP_A : k == 1 ? CP_DT : k < 5 ? CP_C + (k - 2) : k == 5 ? CP_K0 : CP_INVN];
 }
 
 // Shared-memory bytes a launch of the cell kernel needs (dynamic part).
@@ -894,23 +895,29 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
                 }
                 // x <- V0 + f (x - V1) = f x + (V0 - f V1), with V = c + S1 / n and
-                // K = S2 - |S1|^2 / n from the double sums (no division in double);
-                // f and the offsets in the working precision, which they scale
+                // K = S2 - |S1|^2 / n.  The sums are double; the scalars are formed in
+                // the working precision, which they scale (the centred sums keep
+                // |S1|^2 / n small against S2, so no cancellation).  Thread 0 does
+                // this alone while the CTA waits.
                 if (tid == 0) {
-                    const double inv_n = s_cp[CP_INVN];
-                    const double c[3] = {(double)cx, (double)cy, (double)cz};
-                    double K0, V0[3];
+                    const T inv_n = cell_scalar<T>(s_cp, 6);
+                    T St[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) St[q] = (T)s_tot[q];
+                    T K0, V0[3];
                     if (pre_mom) {
-                        K0 = s_cp[CP_K0];
-                        for (int q = 0; q < 3; ++q) V0[q] = s_cp[CP_C + q];
+                        K0 = cell_scalar<T>(s_cp, 5);
+                        V0[0] = cx; V0[1] = cy; V0[2] = cz;
                     } else {
-                        K0 = s_tot[7] - (s_tot[4] * s_tot[4] + s_tot[5] * s_tot[5] + s_tot[6] * s_tot[6]) * inv_n;
-                        for (int q = 0; q < 3; ++q) V0[q] = c[q] + s_tot[4 + q] * inv_n;
+                        K0 = St[7] - (St[4] * St[4] + St[5] * St[5] + St[6] * St[6]) * inv_n;
+                        V0[0] = cx + St[4] * inv_n; V0[1] = cy + St[5] * inv_n; V0[2] = cz + St[6] * inv_n;
                     }
-                    const double K1 = s_tot[3] - (s_tot[0] * s_tot[0] + s_tot[1] * s_tot[1] + s_tot[2] * s_tot[2]) * inv_n;
-                    const T f = (K1 > 0.0 && K0 > 0.0) ? Math<T>::sqrt((T)K0 / (T)K1) : T(1);
+                    const T K1 = St[3] - (St[0] * St[0] + St[1] * St[1] + St[2] * St[2]) * inv_n;
+                    const T f = (K1 > T(0) && K0 > T(0)) ? Math<T>::sqrt(K0 / K1) : T(1);
                     s_par[4] = f;
-                    for (int q = 0; q < 3; ++q) s_par[5 + q] = (T)V0[q] - f * (T)(c[q] + s_tot[q] * inv_n);
+                    s_par[5] = V0[0] - f * (cx + St[0] * inv_n);
+                    s_par[6] = V0[1] - f * (cy + St[1] * inv_n);
+                    s_par[7] = V0[2] - f * (cz + St[2] * inv_n);
                 }
                 __syncthreads();
                 const V2 F = P::make(s_par[4], s_par[4]);

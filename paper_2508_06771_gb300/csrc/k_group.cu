@@ -89,7 +89,9 @@ __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
     f[0] = (float)o[CP_A];
     f[1] = (float)dtj;
     for (int q = 0; q < 3; ++q) f[2 + q] = (float)mean[q];
-    f[5] = 0.0f;
+    f[5] = (float)K0;
+    f[6] = (float)o[CP_INVN];
+    f[7] = 0.0f;
 }
 
 static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,

@@ -54,7 +54,7 @@ enum : int {
     CP_C = 3,        // 3..5: mean velocity of the cell (restoration target and centring shift)
     CP_INVN = 6,     // 1 / N_j
     CP_LNL = 7,      // Coulomb logarithm used
-    CP_F32 = 8,      // 8..10: A, dt and the mean velocity rounded to binary32 (five floats)
+    CP_F32 = 8,      // 8..11: binary32 copies of A, dt, the mean velocity, K0 and 1 / N_j (seven floats)
     NCP = 12
 };
 struct CellParamArgs {
