@@ -1162,21 +1162,30 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             prefetch_l2(a.vy + next_l0, (size_t)cnt * sizeof(T));
             prefetch_l2(a.vz + next_l0, (size_t)cnt * sizeof(T));
         }
-        // ---- 6. write velocities back through the id list (coalesced); the ids
-        // are read back from shared memory next to the velocities, so that they
-        // need not stay in registers through the collision phases
+        // ---- 6. write velocities back.  A single CTA goes through its home
+        // particles (coalesced global stores; ids and positions read back from
+        // shared memory and registers).  A cluster CTA writes the positions it
+        // owns straight to their ids: scattered global stores, which the L2
+        // merges, cost far less than reading another CTA's shared memory at
+        // random positions.
+        if constexpr (C == 1) {
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t k = tid + (uint32_t)i * NT;
-            if (k < nh) {
-                const uint32_t pos = (hq[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                uint32_t p0;
-                const uint32_t o = PB.locate(pos, p0);
-                const uint32_t lp = pos - p0;
-                const uint32_t l = *Cl<C>::at(sl + lp, o);
-                a.vx[l] = *Cl<C>::at(svx + lp, o);
-                a.vy[l] = *Cl<C>::at(svy + lp, o);
-                a.vz[l] = *Cl<C>::at(svz + lp, o);
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t k = tid + (uint32_t)i * NT;
+                if (k < nh) {
+                    const uint32_t pos = (hq[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                    const uint32_t l = sl[pos];
+                    a.vx[l] = svx[pos];
+                    a.vy[l] = svy[pos];
+                    a.vz[l] = svz[pos];
+                }
+            }
+        } else {
+            for (uint32_t q = tid; q < nloc; q += NT) {
+                const uint32_t l = sl[q];
+                a.vx[l] = svx[q];
+                a.vy[l] = svy[q];
+                a.vz[l] = svz[q];
             }
         }
         if constexpr (C > 1) {
