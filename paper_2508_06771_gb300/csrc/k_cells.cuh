@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         pc.mark(2);
         // ---- 1d. place (key, id) at bucket start + slot, in the position-owner CTA.
         // SB: a particle alone in its bucket has its final position already.
-        uint32_t multi = 0u;           // SB: items whose bucket holds several entries
+        uint32_t multi = 0u;           // items whose bucket holds several entries
         if constexpr (SB) {
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
@@ -682,25 +682,35 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 }
             }
         } else {
+            // clusters: the bucket's start and end are read once here (remote);
+            // a particle alone in its bucket is final, the others are placed and
+            // keep (start, size) for the ranking, which then reads only entries
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t k = tid + (uint32_t)i * NT;
-            if (k < nh) {
-                const uint32_t b = hp[i] >> 16, slot = hp[i] & 0xFFFFu;
-                uint32_t b0;
-                const uint32_t ro = BB.locate(b, b0);
-                const uint32_t gpos = *Cl<C>::at(bcnt + (b - b0), ro) + slot;
-                if (gpos < n) {
-                    uint32_t p0;
-                    const uint32_t po = PB.locate(gpos, p0);
-                    const uint32_t lp = gpos - p0;
-                    *Cl<C>::at(ekl + lp, po) = make_uint2(stg[k], hl[i]);
-                } else {
-                    flag_error(ds, ERR_INDEX);
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t k = tid + (uint32_t)i * NT;
+                if (k < nh) {
+                    const uint32_t b = hp[i] >> 16, slot = hp[i] & 0xFFFFu;
+                    uint32_t b0;
+                    const uint32_t ro = BB.locate(b, b0);
+                    const uint32_t* bc = Cl<C>::at(bcnt + (b - b0), ro);   // bc[1]: the next bucket's start
+                    const uint32_t bs = bc[0], be = bc[1];
+                    if (bs + slot < be && be <= n && be - bs < 65536u) {
+                        if (be - bs == 1u) {
+                            hp[i] = bs | ((uint32_t)sw[k] << 16);
+                        } else {
+                            const uint32_t gpos = bs + slot;
+                            uint32_t p0;
+                            const uint32_t po = PB.locate(gpos, p0);
+                            *Cl<C>::at(ekl + (gpos - p0), po) = make_uint2(stg[k], hl[i]);
+                            hp[i] = bs | ((be - bs) << 16);
+                            multi |= 1u << i;
+                        }
+                    } else {
+                        flag_error(ds, ERR_INDEX);
+                        hp[i] = 0u;
+                    }
                 }
-                hp[i] = gpos;
             }
-        }
         }
         Cl<C>::sync();
 
@@ -736,33 +746,20 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             }
         } else {
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t k = tid + (uint32_t)i * NT;
-            if (k < nh) {
-                const uint32_t key = stg[k], l = hl[i];
-                const unsigned long long me = ((unsigned long long)key << 32) | l;
-                const uint32_t b = __umulhi(key, nb);
-                uint32_t b0;
-                const uint32_t ro = BB.locate(b, b0);
-                const uint32_t* bc = Cl<C>::at(bcnt + (b - b0), ro);
-                const uint32_t bs = bc[0], be = bc[1];
-                uint32_t rank = 0u;
-                if (bs <= be && be <= n) {
-                    if (be - bs > 1u) {   // a bucket of one entry holds only this particle
+            for (int i = 0; i < ITEMS; ++i) {
+                if (multi & (1u << i)) {
+                    const uint32_t k = tid + (uint32_t)i * NT;
+                    const unsigned long long me = ((unsigned long long)stg[k] << 32) | hl[i];
+                    const uint32_t bs = hp[i] & 0xFFFFu, be = bs + (hp[i] >> 16);   // checked in 1d
+                    uint32_t rank = 0u;
 #pragma unroll
-                        for (uint32_t u = 0; u < 4u; ++u) {
-                            if (bs + u < be) rank += entry(bs + u) < me ? 1u : 0u;
-                        }
-                        for (uint32_t t = bs + 4u; t < be; ++t) rank += entry(t) < me ? 1u : 0u;
+                    for (uint32_t u = 0; u < 4u; ++u) {
+                        if (bs + u < be) rank += entry(bs + u) < me ? 1u : 0u;
                     }
-                } else {
-                    flag_error(ds, ERR_INDEX);
+                    for (uint32_t t = bs + 4u; t < be; ++t) rank += entry(t) < me ? 1u : 0u;
+                    hp[i] = (bs + rank) | ((uint32_t)sw[k] << 16);
                 }
-                uint32_t pos = bs + rank;
-                if (pos >= n) { flag_error(ds, ERR_INDEX); pos = 0u; }
-                hp[i] = pos | ((uint32_t)sw[k] << 16);
             }
-        }
         }
         Cl<C>::sync();
 
