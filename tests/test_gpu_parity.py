@@ -294,6 +294,45 @@ def test_capacity_overflow_reported(L):
     assert col.sync_code() == L.ECAPACITY
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_restoration_after_rolled_back_append(L, orc, prec):
+    """After a capacity error the stored moments count secondaries that were never appended, so
+    the next Coulomb pass cannot take the restoration's state before S1 from them: it sums the
+    velocities itself.  That pass, with the restoration on, against the oracle from the same
+    state: FP64 velocities within 1e-12, FP32 moments within 1e-5."""
+    wl = W.ragged(M=4, mean_ppc=500, seed=2, T_eV=60.0, with_empty=False)
+    wl["dt_cell"] = np.full(4, 2e-10)
+    if prec == "f32":
+        for k in ("vx", "vy", "vz"):
+            wl[k] = wl[k].astype(np.float32).astype(np.float64)
+    col = L.Collider.from_workload(wl, precision=L.F64 if prec == "f64" else L.F32, capacity=wl["vx"].size,
+                                   correction=1)
+    col.load_workload(wl)
+    col.collide_neutral(col.dt, 0)
+    assert col.sync_code() == L.ECAPACITY
+    vx, vy, vz, cell, _ = col.read()
+    counts = np.bincount(cell, minlength=wl["M"])
+    stored, _ = col.moments()
+    assert (stored[:, 0] != counts).any(), "the stored counts should include the dropped secondaries"
+    st = orc.State(dict(wl, vx=vx.astype(np.float64), vy=vy.astype(np.float64), vz=vz.astype(np.float64),
+                        cell=cell))
+    P = orc.make_params(wl, correction=True)
+    col.collide_coulomb(col.dt, 1)
+    orc.coulomb(st, P, 1)
+    assert col.sync_code() == 0
+    if prec == "f64":
+        gx, gy, gz, _, _ = col.read()
+        err = _vel_err((gx, gy, gz), (st.vx[:st.n], st.vy[:st.n], st.vz[:st.n]))
+        assert err.max() <= FP64_TOL, (err.max(), int(err.argmax()))
+    else:
+        omom, _ = orc.moments(st, P)
+        mom, _ = col.moments()
+        vth = math.sqrt(2.0 * 60.0 * W.E_CHARGE / W.M_E)
+        e = _moment_errors(mom, omom, vth)
+        assert e[:, 0].max() == 0
+        assert e[:, 2:9].max() <= FP32_TOL, e[:, 2:9].max(axis=0)
+
+
 def test_bad_cell_and_nonfinite_rejected(L):
     wl = W.ragged(M=5, mean_ppc=20, seed=1, with_empty=False)
     col = L.Collider.from_workload(wl, precision=L.F64)
