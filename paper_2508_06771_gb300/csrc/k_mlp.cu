@@ -336,28 +336,40 @@ __global__ void k_mlp_init(float* __restrict__ w, uint64_t seed)
 // Features of every cell from its moments (10 sums + 64-bin histogram):
 // 64 bin fractions, log10 n_e, mean energy [eV]; normalised with (x - mean)/std.
 // Targets: k_ion = sum sigma_ion|v| / N, k_el = sum sigma_el|v| / N [m^3/s].
-__global__ void k_mlp_features(int M, const double* __restrict__ mom, const uint32_t* __restrict__ hist,
-                               const double* __restrict__ mom_dens, const double* __restrict__ inv_vol, double weight,
-                               double half_m_over_e,
-                               const float* __restrict__ fmean, const float* __restrict__ fistd, int normalize,
-                               float* __restrict__ Xo, float* __restrict__ To)
+// One warp per cell (lane l: bins l and l + 32; lanes 0 and 1 the last two
+// features and the targets).  The features are binary32, so they are formed
+// in binary32 from one reciprocal of N (binary64 divisions per feature ran on
+// this GPU's narrow FP64 pipe).
+constexpr int FEAT_WARPS = 4;
+__global__ void __launch_bounds__(32 * FEAT_WARPS)
+k_mlp_features(int M, const double* __restrict__ mom, const uint32_t* __restrict__ hist,
+               const double* __restrict__ mom_dens, const double* __restrict__ inv_vol, double weight,
+               double half_m_over_e,
+               const float* __restrict__ fmean, const float* __restrict__ fistd, int normalize,
+               float* __restrict__ Xo, float* __restrict__ To)
 {
-    const int j = blockIdx.x;
-    const int c = threadIdx.x;     // 0..DIN-1
-    if (j >= M || c >= DIN) return;
+    const int j = blockIdx.x * FEAT_WARPS + (int)(threadIdx.x >> 5);
+    const int lane = (int)(threadIdx.x & 31u);
+    if (j >= M) return;
     const double* m = mom + (size_t)j * NMOM;
     const double N = m[0];
-    double f;
-    if (c < NBIN) f = N > 0 ? (double)hist[(size_t)j * NBIN + c] / N : 0.0;
-    else if (c == NBIN) {
+    const float iN = N > 0.0 ? 1.0f / (float)N : 0.0f;
+    float* X = Xo + (size_t)j * DIN;
+    auto put = [&](int c, float x) {
+        if (normalize) x = (x - fmean[c]) * fistd[c];
+        X[c] = x;
+    };
+    const uint32_t* hj = hist + (size_t)j * NBIN;
+    put(lane, (float)hj[lane] * iN);
+    put(lane + 32, (float)hj[lane + 32] * iN);
+    if (lane == 0) {
         const double Nd = mom_dens ? mom_dens[(size_t)j * NMOM] : N;   // density from the whole cell
-        f = Nd > 0 ? log10(weight * Nd * inv_vol[j]) : 0.0;
+        put(NBIN, Nd > 0 ? log10f((float)(weight * Nd * inv_vol[j])) : 0.0f);
+        if (To) To[(size_t)j * DOUT + 0] = (float)m[9] * iN;
+    } else if (lane == 1) {
+        put(NBIN + 1, (float)(half_m_over_e * (m[5] + m[6] + m[7])) * iN);
+        if (To) To[(size_t)j * DOUT + 1] = (float)m[8] * iN;
     }
-    else f = N > 0 ? half_m_over_e * (m[5] + m[6] + m[7]) / N : 0.0;
-    float x = (float)f;
-    if (normalize) x = (x - fmean[c]) * fistd[c];
-    Xo[(size_t)j * DIN + c] = x;
-    if (To && c < DOUT) To[(size_t)j * DOUT + c] = N > 0 ? (float)(m[c == 0 ? 9 : 8] / N) : 0.f;
 }
 
 // Features of a random subsample of each cell: particle l of cell j is kept
@@ -629,7 +641,7 @@ extern "C" int ltpc_mlp_features(ltpc_ctx* ctx, ltpc_mlp* p, float* d_X, float* 
     cudaStream_t s;
     int rc = ltpc_internal_moments_view(ctx, &mom, &hist, &inv, &M, &w, &hme, &s);
     if (rc) return rc;
-    k_mlp_features<<<M, 96, 0, s>>>(M, mom, hist, nullptr, inv, w, hme, p->fmean, p->fistd, normalize, d_X, d_T);
+    k_mlp_features<<<(M + FEAT_WARPS - 1) / FEAT_WARPS, 32 * FEAT_WARPS, 0, s>>>(M, mom, hist, nullptr, inv, w, hme, p->fmean, p->fistd, normalize, d_X, d_T);
     return cudaGetLastError() == cudaSuccess ? LTPC_OK : LTPC_ECUDA;
 }
 
@@ -650,7 +662,7 @@ extern "C" int ltpc_mlp_infer(ltpc_ctx* ctx, ltpc_mlp* p, float* d_rates)
     int rc = ltpc_internal_moments_view(ctx, &mom, &hist, &inv, &M, &w, &hme, &s);
     if (rc) return rc;
     if (M > p->batch_max && M > p->M_max) return LTPC_EINVAL;
-    k_mlp_features<<<M, 96, 0, s>>>(M, mom, hist, nullptr, inv, w, hme, p->fmean, p->fistd, 1, p->xbuf, nullptr);
+    k_mlp_features<<<(M + FEAT_WARPS - 1) / FEAT_WARPS, 32 * FEAT_WARPS, 0, s>>>(M, mom, hist, nullptr, inv, w, hme, p->fmean, p->fistd, 1, p->xbuf, nullptr);
     if (cudaGetLastError() != cudaSuccess) return LTPC_ECUDA;
     // forward in batches of batch_max rows
     cudaStream_t keep = p->stream;
@@ -698,6 +710,6 @@ extern "C" int ltpc_mlp_subsample_features(ltpc_ctx* ctx, ltpc_mlp* p, int32_t p
     k_sub_to_moments<<<(M + 255) / 256, 256, 0, s>>>(M, p->sub, p->subm);
     // the distribution features and the direct rate estimate come from the sample only; the
     // density feature is the cell's density (known exactly from its count)
-    k_mlp_features<<<M, 96, 0, s>>>(M, p->subm, p->subh, mom, inv, w, hme, p->fmean, p->fistd, 1, d_X, d_rates_direct);
+    k_mlp_features<<<(M + FEAT_WARPS - 1) / FEAT_WARPS, 32 * FEAT_WARPS, 0, s>>>(M, p->subm, p->subh, mom, inv, w, hme, p->fmean, p->fistd, 1, d_X, d_rates_direct);
     return cudaGetLastError() == cudaSuccess ? LTPC_OK : LTPC_ECUDA;
 }
