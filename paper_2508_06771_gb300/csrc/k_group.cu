@@ -95,7 +95,8 @@ __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
 }
 
 static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
-                                 uint32_t* __restrict__ perm, const DevState* __restrict__ ds, CellParamArgs cp)
+                                 uint32_t* __restrict__ perm, const DevState* __restrict__ ds, CellParamArgs cp,
+                                 const uint32_t* __restrict__ run_start, const uint32_t* __restrict__ cell_start)
 {
     if (cp.cpar) {                                   // this pass's per-cell scalars, one thread per cell
         const double dt = ds->dt;
@@ -104,6 +105,7 @@ static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __rest
     }
     if (ds->grouping_valid) return;                  // cached grouping: perm is current
     const unsigned long long n = ds->n;
+    const unsigned long long n_sorted = ds->n_sorted;   // particles below lie in their cell's run
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long w0 = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -123,8 +125,12 @@ static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __rest
         const bool same = c[0] == c0 && c[1] == c0 && c[2] == c0 && c[3] == c0;
         if (__all_sync(0xFFFFFFFFu, same) && c0 >= 0) {           // one cell, 128 particles
             uint32_t b = 0u;
-            if (lane == 0) b = atomicAdd(&cursor[c0], 128u);
-            b = __shfl_sync(0xFFFFFFFFu, b, 0) + 4u * lane;
+            if (base + 128ull <= n_sorted) {                      // in the cell's run: no atomic
+                b = cell_start[c0] + (uint32_t)(base - run_start[c0]) + 4u * lane;
+            } else {
+                if (lane == 0) b = atomicAdd(&cursor[c0], 128u);
+                b = __shfl_sync(0xFFFFFFFFu, b, 0) + 4u * lane;
+            }
             const uint32_t l = (uint32_t)l0;
             if ((b & 3u) == 0u) {
                 *reinterpret_cast<uint4*>(perm + b) = make_uint4(l, l + 1u, l + 2u, l + 3u);
@@ -135,12 +141,18 @@ static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __rest
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {                             // mixed cells
-            const unsigned peers = __match_any_sync(0xFFFFFFFFu, c[u]);
+            const unsigned long long l = l0 + u;
+            int32_t ca = c[u];
+            if (ca >= 0 && l < n_sorted) {                        // in its cell's run
+                perm[cell_start[ca] + (uint32_t)(l - run_start[ca])] = (uint32_t)l;
+                ca = -1;
+            }
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, ca);
             const unsigned leader = __ffs(peers) - 1;
             uint32_t b = 0u;
-            if (lane == leader && c[u] >= 0) b = atomicAdd(&cursor[c[u]], (uint32_t)__popc(peers));
+            if (lane == leader && ca >= 0) b = atomicAdd(&cursor[ca], (uint32_t)__popc(peers));
             b = __shfl_sync(0xFFFFFFFFu, b, leader);
-            if (c[u] >= 0) perm[b + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)(l0 + u);
+            if (ca >= 0) perm[b + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)l;
         }
     }
 }
@@ -148,7 +160,7 @@ static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __rest
 // Single-CTA bookkeeping between passes (REGROUP_THREADS threads):
 //   1. if `append`: exclusive scan of this pass's secondaries per cell into
 //      ion_off, capacity check, counts += ion_count, keep the old offsets;
-//   2. CCS2: cell_start = exclusive scan of counts, cursor = cell_start;
+//   2. CCS2: cell_start = exclusive scan of counts, cursor = cell_start + run_len;
 //   3. cluster-class work lists (cells in ascending index order per class,
 //      each item {cell, N_j, I_j, 1} so that a CTA fetches it with one load);
 //   4. reset the work tickets, optionally advance the step number.
@@ -226,7 +238,7 @@ k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_
         uint32_t ex = block_scan(sum, &tot);
         for (uint32_t c = b0; c < b1; ++c) {
             cell_start[c] = ex;
-            cursor[c] = ex;
+            cursor[c] = ex + lists.run_len[c];   // appended particles follow the cell's run
             ex += counts[c];
         }
         if (tid == 0) cell_start[M] = tot;
@@ -326,9 +338,50 @@ static __global__ void k_append(int32_t M, const uint32_t* __restrict__ ion_off,
     }
 }
 
+// Runs of a load (RegroupLists::run_start / run_len).  The load is grouped by
+// cell when every cell id is valid and the ids never decrease; then the run of
+// cell c starts at the first index holding c and has its N_j particles, and
+// the scatter places them without atomics.  Otherwise there are no runs.
+static __global__ void k_runs_check(const int32_t* __restrict__ cell, int32_t M, DevState* ds)
+{
+    const unsigned long long n = ds->n;
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+         l += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t c = cell[l];
+        if (c < 0 || c >= M || (l + 1 < n && cell[l + 1] < c)) {
+            atomicOr(&ds->load_unsorted, 1u);
+            return;
+        }
+    }
+}
+
+static __global__ void k_runs_set(const int32_t* __restrict__ cell, int32_t M, const uint32_t* __restrict__ counts,
+                                  uint32_t* __restrict__ run_start, uint32_t* __restrict__ run_len, DevState* ds)
+{
+    const unsigned long long n = ds->n;
+    const bool grouped = ds->load_unsorted == 0u;
+    const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long c = gt; c < (unsigned long long)M; c += stride) run_len[c] = grouped ? counts[c] : 0u;
+    if (grouped) {
+        for (unsigned long long l = gt; l < n; l += stride) {
+            const int32_t c = cell[l];
+            if (l == 0 || cell[l - 1] != c) run_start[c] = (uint32_t)l;
+        }
+    }
+    if (gt == 0) ds->n_sorted = grouped ? n : 0ull;
+}
+
+static __global__ void k_reset_cursors(int32_t M, const uint32_t* __restrict__ cell_start,
+                                       const uint32_t* __restrict__ run_len, uint32_t* __restrict__ cursor)
+{
+    for (int32_t c = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); c < M; c += (int32_t)(gridDim.x * blockDim.x))
+        cursor[c] = cell_start[c] + run_len[c];
+}
+
 static __global__ void k_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step)
 {
-    if (set_n) { ds->n = n; ds->n_ion = 0u; ds->grouping_valid = 0u; }
+    if (set_n) { ds->n = n; ds->n_ion = 0u; ds->grouping_valid = 0u; ds->load_unsorted = 0u; ds->n_sorted = 0ull; }
     if (set_step) { ds->step = step; ds->dt = dt; }
 }
 
@@ -353,10 +406,11 @@ cudaError_t launch_hist(const int32_t* cell, uint32_t* counts, int32_t M, DevSta
 }
 
 cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uint32_t* perm, const DevState* ds,
-                           int grid, cudaStream_t s, const CellParamArgs* cp)
+                           int grid, cudaStream_t s, const RegroupLists& runs, const uint32_t* cell_start,
+                           const CellParamArgs* cp)
 {
     CellParamArgs none = {};
-    k_scatter<<<grid, 256, 0, s>>>(cell, M, cursor, perm, ds, cp ? *cp : none);
+    k_scatter<<<grid, 256, 0, s>>>(cell, M, cursor, perm, ds, cp ? *cp : none, runs.run_start, cell_start);
     return cudaGetLastError();
 }
 
@@ -383,6 +437,21 @@ template cudaError_t launch_append<float>(int32_t, const uint32_t*, const uint32
 template cudaError_t launch_append<double>(int32_t, const uint32_t*, const uint32_t*, const uint32_t*,
                                            const double*, const double*, const double*, double*, double*, double*,
                                            int32_t*, double*, const DevState*, int, cudaStream_t);
+
+cudaError_t launch_runs(const int32_t* cell, int32_t M, const uint32_t* counts, const RegroupLists& runs, DevState* ds,
+                        int grid, cudaStream_t s)
+{
+    k_runs_check<<<grid, 256, 0, s>>>(cell, M, ds);
+    k_runs_set<<<grid, 256, 0, s>>>(cell, M, counts, runs.run_start, runs.run_len, ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_cursors(int32_t M, const uint32_t* cell_start, const RegroupLists& runs, uint32_t* cursor,
+                                 cudaStream_t s)
+{
+    k_reset_cursors<<<(M + 255) / 256, 256, 0, s>>>(M, cell_start, runs.run_len, cursor);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step,
                              cudaStream_t s)

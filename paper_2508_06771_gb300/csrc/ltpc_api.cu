@@ -31,7 +31,7 @@ struct Layout {
     size_t vx, vy, vz, cell, x;
     // work offsets
     size_t perm, counts, cell_start, cs_prev, cursor, ion_count, ion_off, stage_l, stage_vx, stage_vy,
-        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, lists, ds;
+        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, lists, ds;
 };
 
 bool compute_layout(const ltpc_config* c, Layout* L)
@@ -66,6 +66,8 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->dt_factor = take(M * 8);
     L->lnlam = take(M * 8);
     L->cpar = take(M * NCP * 8);
+    L->run_start = take(M * 4);
+    L->run_len = take(M * 4);
     L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
     L->work = o;
@@ -128,6 +130,8 @@ int set_table(ltpc_ctx* ctx, int table)
     ctx->grid.assign(T.n, 0);
     ctx->lists.n_classes = T.n;
     ctx->lists.cache_grouping = ctx->cfg.cache_grouping;
+    ctx->lists.run_start = ctx->w<uint32_t>(ctx->L.run_start);
+    ctx->lists.run_len = ctx->w<uint32_t>(ctx->L.run_len);
     for (int k = 0; k < MAX_CLASSES; ++k) {
         ctx->lists.max_n[k] = 0;
         ctx->lists.list[k] = ctx->w<uint4>(ctx->L.lists) + (size_t)k * ctx->cfg.n_cells;
@@ -211,7 +215,7 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
     cp.e_over_m = ctx->cfg.charge / ctx->cfg.mass;
     cp.lnl_nrl = ctx->cfg.lnlambda_mode == LTPC_LNL_NRL ? 1 : 0;
     CK(launch_scatter(ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
-                      grid_stream, s, &cp));
+                      grid_stream, s, ctx->lists, ctx->w<uint32_t>(L.cell_start), &cp));
     CK(mark());
     CellArgs<T> a = make_args<T>(ctx, flags);
     a.order_out = order_out;
@@ -440,6 +444,8 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
                                        ctx->sms * 4, s));
     int rc = async ? LTPC_OK : read_errors(ctx);
     if (rc) return rc;
+    CK(launch_runs(ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(L.counts), ctx->lists, ctx->ds,
+                   ctx->sms * 8, s));
     CK(launch_regroup(ctx->cfg.n_cells, ctx->w<uint32_t>(L.counts), ctx->w<uint32_t>(L.cell_start),
                       ctx->w<uint32_t>(L.cs_prev), ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.ion_count),
                       ctx->w<uint32_t>(L.ion_off), ctx->lists, (unsigned long long)ctx->cfg.capacity, 0, 0, ctx->ds,
@@ -599,10 +605,10 @@ int ltpc_grouping(ltpc_ctx* ctx, uint32_t* d_cell_start, uint32_t* d_perm, uint3
     const size_t M = (size_t)ctx->cfg.n_cells;
     // the grouping of the current particles: redo CCS3 into perm
     CK(launch_scatter(ctx->s<int32_t>(ctx->L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(ctx->L.cursor), ctx->w<uint32_t>(ctx->L.perm),
-                      ctx->ds, ctx->sms * 8, ctx->stream));
+                      ctx->ds, ctx->sms * 8, ctx->stream, ctx->lists, ctx->w<uint32_t>(ctx->L.cell_start)));
     // restore the cursors for the next pass
-    CK(cudaMemcpyAsync(ctx->w<uint32_t>(ctx->L.cursor), ctx->w<uint32_t>(ctx->L.cell_start), M * 4,
-                       cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(launch_reset_cursors(ctx->cfg.n_cells, ctx->w<uint32_t>(ctx->L.cell_start), ctx->lists,
+                            ctx->w<uint32_t>(ctx->L.cursor), ctx->stream));
     if (d_cell_start)
         CK(cudaMemcpyAsync(d_cell_start, ctx->w<uint32_t>(ctx->L.cell_start), (M + 1) * 4, cudaMemcpyDeviceToDevice,
                            ctx->stream));

@@ -41,6 +41,8 @@ struct DevState {
     unsigned int n_ion;               // secondaries appended by the last pass
     unsigned int max_count;           // largest cell at the last regrouping
     unsigned int grouping_valid;      // 1: perm still groups the particles (no load, no append since)
+    unsigned int load_unsorted;       // 1: the loaded storage is not grouped by cell
+    unsigned long long n_sorted;      // particles [0, n_sorted) lie in per-cell runs (cell-grouped load)
 };
 
 // Per-cell scalars of one pass, formed by a grid-wide loop at the start of

@@ -15,6 +15,12 @@ struct RegroupLists {
     uint32_t max_n[MAX_CLASSES];   // largest cell of each class
     uint4* list[MAX_CLASSES];      // device work lists (M entries each): {cell, N_j, I_j, 1}
     int32_t cache_grouping;        // 1: skip CCS3 while the grouping is unchanged
+    // Runs of a cell-grouped load: the loaded particles of cell c occupy
+    // [run_start[c], run_start[c] + run_len[c]) (run_len 0 when the load was not
+    // grouped by cell).  They take the first run_len[c] places of the cell's
+    // grouping in index order; appended particles follow.
+    uint32_t* run_start;
+    uint32_t* run_len;
 };
 
 // One compiled shape of the cell kernel.
@@ -51,7 +57,12 @@ int class_tables(int precision, const ClassTable** out);
 // Host-side launchers of the grouping / bookkeeping kernels (k_group.cu).
 cudaError_t launch_hist(const int32_t* cell, uint32_t* counts, int32_t M, DevState* ds, int grid, cudaStream_t s);
 cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uint32_t* perm, const DevState* ds, int grid,
-                           cudaStream_t s, const CellParamArgs* cp = nullptr);
+                           cudaStream_t s, const RegroupLists& runs, const uint32_t* cell_start,
+                           const CellParamArgs* cp = nullptr);
+cudaError_t launch_runs(const int32_t* cell, int32_t M, const uint32_t* counts, const RegroupLists& runs, DevState* ds,
+                        int grid, cudaStream_t s);
+cudaError_t launch_reset_cursors(int32_t M, const uint32_t* cell_start, const RegroupLists& runs, uint32_t* cursor,
+                                 cudaStream_t s);
 cudaError_t launch_regroup(int32_t M, uint32_t* counts, uint32_t* cell_start, uint32_t* cs_prev, uint32_t* cursor,
                            uint32_t* ion_count, uint32_t* ion_off, const RegroupLists& lists,
                            unsigned long long capacity, int append, int advance_step, DevState* ds, cudaStream_t s);
