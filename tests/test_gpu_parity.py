@@ -81,6 +81,35 @@ def test_grouping_and_pair_order_bit_exact(L, orc, prec):
     col.sync()
 
 
+@pytest.mark.parametrize("shuffled", [False, True])
+def test_grouping_after_appends(L, orc, shuffled):
+    """CCS1-CCS3 after ionization appends: for storage loaded in cell order the loaded particles
+    are placed from their cell's run and the appended ones from the cell's cursor; for shuffled
+    storage all take the cursor.  Either way each cell's segment holds exactly its particles, and
+    the pairing order matches the oracle's."""
+    wl = W.ragged(M=24, mean_ppc=400, seed=9, T_eV=30.0, shuffled=shuffled)
+    wl["dt_cell"] = np.full(wl["M"], 5e-11)
+    col = L.Collider.from_workload(wl, precision=L.F64)
+    col.load_workload(wl)
+    n0 = col.count()
+    for s in range(3):
+        col.step(col.dt, s)
+    col.sync()
+    assert col.count() > n0, "no secondaries appended"
+    _, _, _, cell, _ = col.read()
+    cs, perm, cnt = col.grouping()
+    ocounts, ocs, operm = orc.group(cell, wl["M"])
+    assert np.array_equal(cnt, ocounts)
+    assert np.array_equal(cs.astype(np.uint64), ocs)
+    for j in range(wl["M"]):
+        a, b = int(ocs[j]), int(ocs[j + 1])
+        assert np.array_equal(np.sort(perm[a:b]), operm[a:b]), j
+    gcs, gorder = col.pair_order(3)
+    ocs2, oorder = orc.pair_order(cell, wl["M"], wl["seed"], 3)
+    assert np.array_equal(gorder, oorder)
+    col.sync()
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_every_class_table_pairs_bit_exact(L, orc, prec):
     """Every class table (every compiled block/cluster shape in use) gives the
