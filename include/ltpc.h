@@ -112,7 +112,10 @@ void ltpc_destroy(ltpc_ctx* ctx);
  * precision.  flags: LTPC_LOAD_SRC_DEVICE selects device sources (host
  * sources should be pinned for full copy bandwidth); LTPC_LOAD_ASYNC makes
  * the call asynchronous.  Builds the per-cell grouping (CCS1-CCS3) and the
- * moments of the loaded state.
+ * moments of the loaded state.  Storage ordered by cell (cell ids never
+ * decreasing) is recognised: the per-step grouping then places the loaded
+ * particles from their cell's run without atomics (results are the same for
+ * any order).
  * Synchronizing by default.  Errors: EINVAL (n < 0, n > capacity or unknown
  * flags), ECUDA; ENONFINITE and EINVAL for cell ids out of range are reported
  * by this call, or with LTPC_LOAD_ASYNC by the next ltpc_sync (particles
@@ -179,7 +182,10 @@ int ltpc_sync(ltpc_ctx* ctx);
 int ltpc_pair_order(ltpc_ctx* ctx, int64_t step, uint32_t* d_order, uint32_t* d_cell_start);
 
 /* Inspection: the grouping of CCS1-CCS3 (cell_start[M+1], perm[n], counts[M];
- * device pointers, any may be NULL).  Asynchronous. */
+ * device pointers, any may be NULL).  perm[cell_start[j] .. cell_start[j+1])
+ * holds the ids of cell j: after a load ordered by cell, the loaded particles
+ * first in index order, then appended ones; otherwise in unspecified order.
+ * Asynchronous. */
 int ltpc_grouping(ltpc_ctx* ctx, uint32_t* d_cell_start, uint32_t* d_perm, uint32_t* d_counts);
 
 /* Cluster classes used for cells of different sizes: class i handles cells
