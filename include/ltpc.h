@@ -167,6 +167,19 @@ int ltpc_profile_phases(ltpc_ctx* ctx, double dt, int64_t step, unsigned long lo
  * Either pointer may be NULL.  Host destinations synchronize the stream. */
 int ltpc_moments(ltpc_ctx* ctx, double* mom, uint32_t* hist, int dst_is_device);
 
+/* Restore the per-cell moments (same layout as ltpc_moments; hist may be
+ * NULL), typically from a checkpoint.  A pass takes the cell's state before
+ * S1 for the momentum/energy restoration, and the NRL Coulomb logarithm, from
+ * the moments the previous pass left (the paper has no such state: it is this
+ * library's way of not summing the cell twice).  A checkpoint is therefore
+ * (ltpc_read_particles, ltpc_moments, the next step number); resuming with
+ * ltpc_load_particles, then ltpc_set_moments, then the same steps and class
+ * table, reproduces the uninterrupted run bit for bit.  Call it after the
+ * load (which computes moments of its own).  src_is_device: 1 device
+ * pointers, 0 host (the call then synchronizes the stream).  Errors: EINVAL
+ * (NULL ctx or mom), ECUDA. */
+int ltpc_set_moments(ltpc_ctx* ctx, const double* mom, const uint32_t* hist, int src_is_device);
+
 /* Copy the particles out: velocities, cell ids, optional positions (any
  * pointer may be NULL); *n_out receives the particle count.  Synchronizing. */
 int ltpc_read_particles(ltpc_ctx* ctx, void* vx, void* vy, void* vz, int32_t* cell, void* x,

@@ -4,10 +4,13 @@
 // (persistent loop, dynamic tickets).  Per cell it performs, on chip:
 //   1. pairing order (Table 5, reading of "define partner pairs"): every
 //      particle draws a key r_l; the cell's particles are sorted by (r_l, l)
-//      with a bucket sort distributed over the cluster's shared memory;
+//      with a bucket sort distributed over the cluster's shared memory (a
+//      particle alone in its bucket takes its position from the bucket scan);
 //   2. step S1 (Table 2), the Takizuka-Abe collision of consecutive entries
-//      (CCS4-CCS5 of Table 5), with per-cell sums before and after for the
-//      optional momentum/energy restoration;
+//      (CCS4-CCS5 of Table 5), with the optional momentum/energy restoration
+//      from the cell's sums after S1 and its state before S1 (taken from the
+//      per-cell record that the pass's first kernel forms from the stored
+//      moments);
 //   3. step S2a for electron-neutral collisions C1/C2 (Table 1) with the
 //      null-collision method of Sec. 4.2, staging ionization secondaries
 //      (Table 3, CS5) at a deterministic slot;
@@ -18,8 +21,10 @@
 // the same way, single-CTA classes gather the velocities with cp.async
 // straight into pairing order, and the next cell's id list and velocity
 // ranges are brought into L2 while the current cell computes.  Per-cell sums
-// are formed per thread and per warp in the working precision and combined in
-// double.  Index math is in ltpc_index.h.
+// are formed per thread and per warp in the working precision (a pair's two
+// particles in the two lanes of packed binary32 operations) and combined in
+// double.  Cluster CTAs write back the positions they own straight to the
+// particles' ids.  Index math is in ltpc_index.h.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -715,12 +720,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         Cl<C>::sync();
 
         pc.mark(3);
-        // ---- 1e. each home particle ranks itself inside its bucket: its final
-        // pairing-order position is the bucket start plus the number of entries
-        // of the bucket ordered before (key, id).  With one bucket per particle
-        // on average almost every bucket holds at most four entries: those are
-        // loaded and compared together (independent loads, no divergent walk),
-        // and only the rare larger buckets continue serially.
+        // ---- 1e. each particle that shares its bucket ranks itself inside it:
+        // its final pairing-order position is the bucket start plus the number of
+        // entries of the bucket ordered before (key, id).  With half a particle
+        // (single CTAs) or one particle (clusters) per bucket on average, almost
+        // every shared bucket holds at most four entries: those are loaded and
+        // compared together (independent loads, no divergent walk), and only the
+        // rare larger buckets continue serially.
         auto entry = [&](uint32_t t) -> unsigned long long {
             uint32_t t0;
             const uint32_t o = PB.locate(t, t0);

@@ -557,6 +557,17 @@ int ltpc_moments(ltpc_ctx* ctx, double* mom, uint32_t* hist, int dst_is_device)
     return LTPC_OK;
 }
 
+int ltpc_set_moments(ltpc_ctx* ctx, const double* mom, const uint32_t* hist, int src_is_device)
+{
+    if (!ctx || !mom) return LTPC_EINVAL;
+    const size_t M = (size_t)ctx->cfg.n_cells;
+    const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->w<double>(ctx->L.mom), mom, M * NMOM * 8, kind, ctx->stream));
+    if (hist) CK(cudaMemcpyAsync(ctx->w<uint32_t>(ctx->L.hist), hist, M * NBIN * 4, kind, ctx->stream));
+    if (!src_is_device) CK(cudaStreamSynchronize(ctx->stream));
+    return LTPC_OK;
+}
+
 int ltpc_read_particles(ltpc_ctx* ctx, void* vx, void* vy, void* vz, int32_t* cell, void* x, int64_t* n_out,
                         int dst_is_device)
 {

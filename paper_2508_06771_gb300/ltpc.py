@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
             "ltpc_profile_step": (C.c_int, [vp, C.c_double, i64, C.POINTER(C.c_float), i32, C.POINTER(i32)]),
             "ltpc_profile_phases": (C.c_int, [vp, C.c_double, i64, vp]),
             "ltpc_moments": (C.c_int, [vp, vp, vp, C.c_int]),
+            "ltpc_set_moments": (C.c_int, [vp, vp, vp, C.c_int]),
             "ltpc_read_particles": (C.c_int, [vp, vp, vp, vp, vp, vp, C.POINTER(i64), C.c_int]),
             "ltpc_sync": (C.c_int, [vp]),
             "ltpc_pair_order": (C.c_int, [vp, i64, vp, vp]),
@@ -285,6 +286,13 @@ class Collider:
         """Moments straight into host arrays (synchronizing)."""
         self._check(self.L.ltpc_moments(self.ctx, mom.ctypes.data, hist.ctypes.data if hist is not None else None, 0),
                     "moments")
+
+    def set_moments(self, mom: np.ndarray, hist: np.ndarray | None = None):
+        """Restore the per-cell moments from host arrays (a checkpoint's), after a load."""
+        m = np.ascontiguousarray(mom, dtype=np.float64)
+        h = None if hist is None else np.ascontiguousarray(hist, dtype=np.uint32)
+        self._check(self.L.ltpc_set_moments(self.ctx, m.ctypes.data, None if h is None else h.ctypes.data, 0),
+                    "set_moments")
 
     def count(self) -> int:
         n = C.c_int64()
