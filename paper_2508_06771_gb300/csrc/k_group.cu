@@ -43,7 +43,9 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
 //     summed squared peculiar speed K0 = sum |v|^2 - |sum v|^2 / N before the
 //     collisions.  The stored moments are sums over exactly the velocities the
 //     pass starts from when their count equals N_j; otherwise (an append rolled
-//     back by a capacity error) K0 = -1 asks the pass to form the sums itself.
+//     back by a capacity error), or when the cell drifts faster than its thermal
+//     speed (cancellation in the uncentred sums), K0 = -1 asks the pass to form
+//     centred sums itself.
 __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
 {
     // One binary64 division per cell (1 / sum of counts of the stored moments);
@@ -78,8 +80,13 @@ __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
     for (int q = 0; q < 3; ++q) o[CP_C + q] = mean[q];
     double K0 = -1.0;
     if (n > 0u && N == (double)n) {
-        K0 = s2 - (m[2] * mean[0] + m[3] * mean[1] + m[4] * mean[2]);
+        const double drift = m[2] * mean[0] + m[3] * mean[1] + m[4] * mean[2];   // N |mean|^2
+        K0 = s2 - drift;
         K0 = K0 > 0.0 ? K0 : 0.0;
+        // The stored sums are not centred: when the drift energy exceeds the
+        // thermal one, K0 = sum |v|^2 - N |mean|^2 loses digits to cancellation,
+        // so the pass forms centred sums itself instead.
+        if (drift > K0) K0 = -1.0;
         o[CP_INVN] = iN;
     } else {
         o[CP_INVN] = n > 0u ? 1.0 / (double)n : 0.0;

@@ -272,6 +272,46 @@ def test_fp32_coulomb_moments(L, orc):
         assert e[:, 2:9].max() <= FP32_TOL, (s, e[:, 2:9].max(axis=0))
 
 
+def test_fp32_restoration_with_drift(L, orc):
+    """Cells drifting at several times their thermal speed: the restoration's state before S1
+    must not lose digits to the drift (the stored moments are not centred).  Each cell's thermal
+    energy, sum |v - mean|^2 of the read-back velocities, stays within 1e-6 of the FP64
+    oracle's, and the moments within the FP32 bar."""
+    wl = W.tail_4096x10000(M=16, ppc=2000, steps=2)
+    wl["neutral"] = False
+    vth = math.sqrt(2.0 * W.E_CHARGE / W.M_E)
+    wl["vz"] = wl["vz"] + 10.0 * vth
+    wl["vx"] = wl["vx"] - 4.0 * vth
+    for k in ("vx", "vy", "vz"):
+        wl[k] = wl[k].astype(np.float32).astype(np.float64)   # the oracle starts from the same values
+    col = L.Collider.from_workload(wl, precision=L.F32)
+    col.load_workload(wl)
+    st = orc.State(wl)
+    P = orc.make_params(wl, correction=True)
+    for s in range(2):
+        col.collide_coulomb(wl["dt"], s)
+        orc.coulomb(st, P, s)
+    gx, gy, gz, cell, _ = col.read()
+    mom, _ = col.moments()
+    col.sync()
+
+    def thermal(vx, vy, vz):
+        out = np.zeros(wl["M"])
+        for j in range(wl["M"]):
+            sel = cell == j
+            v = np.stack([vx[sel], vy[sel], vz[sel]], 1).astype(np.float64)
+            out[j] = ((v - v.mean(0)) ** 2).sum()
+        return out
+
+    Kg = thermal(gx, gy, gz)
+    Ko = thermal(st.vx[:st.n], st.vy[:st.n], st.vz[:st.n])
+    assert (np.abs(Kg - Ko) / Ko).max() <= 1e-6, (np.abs(Kg - Ko) / Ko).max()
+    omom, _ = orc.moments(st, P)
+    e = _moment_errors(mom, omom, vth)
+    assert e[:, 0].max() == 0
+    assert e[:, 2:9].max() <= FP32_TOL, e[:, 2:9].max(axis=0)
+
+
 def test_fp32_full_step_with_flip_accounting(L, orc):
     wl = W.tail_4096x10000(M=32, ppc=2000, steps=1)
     for k in ("vx", "vy", "vz"):
