@@ -144,9 +144,19 @@ __global__ void __launch_bounds__(NTH) k_mlp_tile(Weights W, const float* __rest
     const int row0 = blockIdx.x * ROWS;
     const int rows = min(ROWS, B - row0);
 
-    // ---- stage weights and inputs (inputs rounded to bf16, padding zero)
-    for (int i = tid; i < H * DINP; i += NTH) S.w1[(i / DINP) * LDX + i % DINP] = W.w1b[i];
-    for (int i = tid; i < H * H; i += NTH) S.w2[(i / H) * LDH + i % H] = W.w2b[i];
+    // ---- stage weights and inputs (inputs rounded to bf16, padding zero).  The
+    // bf16 weight rows move 16 bytes (8 values) at a time: every row of W1, W2
+    // and of their padded shared-memory copies starts on a 16-byte boundary.
+    constexpr int V1 = DINP / 8, V2 = H / 8;          // 16-byte vectors per row
+    static_assert(DINP % 8 == 0 && H % 8 == 0 && LDX % 8 == 0 && LDH % 8 == 0, "16-byte rows");
+    for (int i = tid; i < H * V1; i += NTH) {
+        const int r = i / V1, c = (i % V1) * 8;
+        *reinterpret_cast<uint4*>(&S.w1[r * LDX + c]) = *reinterpret_cast<const uint4*>(W.w1b + r * DINP + c);
+    }
+    for (int i = tid; i < H * V2; i += NTH) {
+        const int r = i / V2, c = (i % V2) * 8;
+        *reinterpret_cast<uint4*>(&S.w2[r * LDH + c]) = *reinterpret_cast<const uint4*>(W.w2b + r * H + c);
+    }
     for (int i = tid; i < DOUT * H; i += NTH) S.w3[i] = W.params[OFF_W3 + i];
     for (int i = tid; i < H; i += NTH) { S.b1[i] = W.params[OFF_B1 + i]; S.b2[i] = W.params[OFF_B2 + i]; }
     if (tid < DOUT) S.b3[tid] = W.params[OFF_B3 + tid];
