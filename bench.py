@@ -473,7 +473,7 @@ def run_ours(args, rank, world, local_rank):
     # step s+1's inputs (the link is the bound) overlaps the kernels of step s.
     e2e = None
     if not args.no_e2e:
-        ne = max(4, min(20, args.steps // 20))
+        ne = max(20, min(60, args.steps // 10))
         host = [torch.from_numpy(np.ascontiguousarray(wl[k], dtype=np.float32 if prec == "f32" else np.float64))
                 .pin_memory() for k in ("vx", "vy", "vz")]
         hcell = torch.from_numpy(np.ascontiguousarray(wl["cell"], dtype=np.int32)).pin_memory()

@@ -10,30 +10,28 @@
 namespace ltpc {
 
 // CCS1 at load time: N_j by warp-aggregated atomics (counts must be zero).
+// The loop runs over whole warps (its bound is rounded up to a multiple of 32
+// and the same for every lane), so every lane takes part in each match with
+// the full mask; a lane past the end or holding an out-of-range id takes part
+// with the sentinel -1 and adds nothing.
 static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __restrict__ counts, int32_t M,
                        DevState* ds)
 {
     const unsigned long long n = ds->n;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += stride) {
-        const int32_t c = cell[l];
-        const unsigned act = __activemask();
-        if (c < 0 || c >= M) {
+    const unsigned long long n_up = (n + 31ull) & ~31ull;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;   // blockDim is a multiple of 32
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n_up; l += stride) {
+        int32_t c = l < n ? cell[l] : -1;
+        if (l < n && (c < 0 || c >= M)) {
             atomicOr(&ds->err, ERR_BAD_CELL);
-            continue;
+            c = -1;
         }
-        const unsigned peers = __match_any_sync(act, c);
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
         const unsigned leader = __ffs(peers) - 1;
-        if ((threadIdx.x & 31u) == leader) atomicAdd(&counts[c], (uint32_t)__popc(peers));
+        if (c >= 0 && (threadIdx.x & 31u) == leader) atomicAdd(&counts[c], (uint32_t)__popc(peers));
     }
 }
 
-// CCS3: perm[I_j + rank] = l.  Cell ids outside [0, M) are skipped (the load's
-// histogram reports them).  With the cached-grouping option the kernel exits
-// at once while the previous grouping still holds.  Each warp takes 128 consecutive particles (4 per
-// lane, 16-byte loads).  When they all belong to one cell -- the usual case for
-// cell-grouped storage -- one cursor atomic serves the 128 and the ids are
-// written with 16-byte stores; otherwise one atomic per warp and cell.
 // The per-cell scalars of a pass (CellParamArgs), from the cell's count, its
 // inputs and the moments left by the previous pass:
 //   * the Takizuka-Abe coefficient A = q^4 n_j lnL dt_j / (8 pi eps0^2 mu^2),
@@ -101,6 +99,14 @@ __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
     f[7] = 0.0f;
 }
 
+// CCS3: perm[I_j + rank] = l.  Cell ids outside [0, M) are skipped (the load's
+// histogram reports them).  With the cached-grouping option the kernel exits
+// at once while the previous grouping still holds.  Each warp takes 128
+// consecutive particles (4 per lane, 16-byte loads).  When they all belong to
+// one cell -- the usual case for cell-grouped storage -- one cursor atomic
+// serves the 128 and the ids are written with 16-byte stores; otherwise one
+// atomic per warp and cell.  The first thing the kernel does is form the
+// per-cell scalars of the pass (cell_params above), one thread per cell.
 static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
                                  uint32_t* __restrict__ perm, const DevState* __restrict__ ds, CellParamArgs cp,
                                  const uint32_t* __restrict__ run_start, const uint32_t* __restrict__ cell_start)

@@ -40,19 +40,25 @@ __global__ void na_clear(uint32_t* scr, int32_t M)
     if (blockIdx.x == 0 && threadIdx.x == 0) scr[kFlagWord] = 0u;
 }
 
+// Both grid-stride loops below run over whole warps: the bound is n rounded up
+// to a multiple of 32 (the block size is a multiple of 32), so all 32 lanes of
+// a warp take every iteration together and call __match_any_sync with the
+// full mask.  A lane past the end, or holding an out-of-range id, joins the
+// match with the sentinel -1 and takes no part in the counting or placing.
+
 // Counts per cell (one atomic per warp and cell); out-of-range ids raise the flag.
 __global__ void na_hist(const int32_t* __restrict__ cell, unsigned long long n, int32_t M, uint32_t* scr)
 {
-    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+    const unsigned long long n_up = (n + 31ull) & ~31ull;
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n_up;
          l += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = cell[l];
-        const unsigned act = __activemask();
-        if (c < 0 || c >= M) {
+        int32_t c = l < n ? cell[l] : -1;
+        if (l < n && (c < 0 || c >= M)) {
             atomicOr(&scr[kFlagWord], 1u);
-            continue;
+            c = -1;
         }
-        const unsigned peers = __match_any_sync(act, c);
-        if ((threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&scr[c], (uint32_t)__popc(peers));
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
+        if (c >= 0 && (threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&scr[c], (uint32_t)__popc(peers));
     }
 }
 
@@ -98,17 +104,17 @@ __global__ void na_scatter(const int32_t* __restrict__ cell, unsigned long long 
                            uint32_t* __restrict__ perm)
 {
     const unsigned lane = threadIdx.x & 31u;
-    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+    const unsigned long long n_up = (n + 31ull) & ~31ull;
+    for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n_up;
          l += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = cell[l];
-        const unsigned act = __activemask();
-        if (c < 0 || c >= M) continue;
-        const unsigned peers = __match_any_sync(act, c);
+        int32_t c = l < n ? cell[l] : -1;
+        if (c < 0 || c >= M) c = -1;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
         const unsigned leader = (unsigned)(__ffs(peers) - 1);
         uint32_t base = 0u;
-        if (lane == leader) base = atomicAdd(&scr[c], (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        perm[base + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)l;
+        if (c >= 0 && lane == leader) base = atomicAdd(&scr[c], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (c >= 0) perm[base + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)l;
     }
 }
 
@@ -149,8 +155,11 @@ extern "C" int ltpc_group_cells_noalloc(const int32_t* d_cell, int64_t n, int32_
     na_scan<<<1, kScanThreads, 0, s>>>(scr, n_cells, d_cell_start);
     na_scatter<<<sms * 4, 256, 0, s>>>(d_cell, nn, n_cells, scr, d_perm);
     if (cudaGetLastError() != cudaSuccess) return LTPC_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return LTPC_ECUDA;
+    // the flag word is read on the caller's stream, then only that stream is
+    // waited for (no device-wide wait on the legacy default stream)
     uint32_t flag = 0u;
-    if (cudaMemcpy(&flag, scr + kFlagWord, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess) return LTPC_ECUDA;
+    if (cudaMemcpyAsync(&flag, scr + kFlagWord, sizeof flag, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return LTPC_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LTPC_ECUDA;
     return flag ? LTPC_EINVAL : LTPC_OK;
 }
