@@ -27,8 +27,10 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-TAG_PARTICLE, TAG_PAIR, TAG_SCATTER, TAG_SECONDARY = 1, 2, 3, 4
+TAG_PARTICLE, TAG_PAIR, TAG_SCATTER, TAG_SECONDARY, TAG_PERM = 1, 2, 3, 4, 5
 OK, EINVAL, ECAPACITY = 0, -1, -2
+PAIR_KEY, PAIR_BIJECTION = 0, 1
+BIJ_MIN_N = 4097          # in the bijection mode, cells of at least this many particles use it
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +55,7 @@ class Params(C.Structure):
         ("weight", C.c_double), ("n_neutral", C.c_double), ("mass_neutral", C.c_double),
         ("sigma_el", C.c_double), ("sigma_ion", C.c_double), ("e_ion", C.c_double),
         ("seed", C.c_uint64), ("odd_mode", C.c_int32), ("correction", C.c_int32),
+        ("pairing_mode", C.c_int32), ("reserved", C.c_int32), ("cell_ids", C.c_void_p),
     ]
 
 
@@ -94,6 +97,9 @@ def lib():
                                       f64p, u32p]
             L.orc_step.argtypes = [i64p, C.c_int64, C.c_int32, i32p, f64p, f64p, f64p, f64p, f64p, f64p,
                                    f64p, C.POINTER(Params), C.c_uint32, C.c_int, C.c_int, f64p, u32p, i64p]
+            L.orc_bij_table.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, u32p, u32p]
+            L.orc_pair_order_mode.argtypes = [C.c_int64, C.c_int32, i32p, u32p, C.POINTER(Params), C.c_uint32,
+                                              u64p, u32p]
             _mlp_argtypes(L)
         return _lib
 
@@ -145,12 +151,43 @@ def pair_order(cell: np.ndarray, M: int, seed: int, step: int):
     return cs, order[:n]
 
 
+def bij_table(seed: int, cell: int, step: int, n: int, inverse: bool = False):
+    """The pairing bijection of a cell of n particles (bijection mode): pi(r) for r in [0, n)
+    (or its inverse), and the parameters (a, b, six round keys, candidate-count word)."""
+    out = np.zeros(max(n, 1), np.uint32)
+    prm = np.zeros(9, np.uint32)
+    _check(lib().orc_bij_table(int(seed), int(cell), int(step) & 0xFFFFFFFF, int(n), 1 if inverse else 0,
+                               _p(out, C.c_uint32), _p(prm, C.c_uint32)))
+    return out[:n], prm
+
+
+def pair_order_mode(cell: np.ndarray, M: int, params: "Params", step: int, ids: np.ndarray | None = None):
+    """Pairing order under the params' pairing mode (key sort, or bijection for large cells)."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    n = cell.size
+    cs = np.zeros(M + 1, dtype=np.uint64)
+    order = np.zeros(max(n, 1), dtype=np.uint32)
+    idp = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint32)
+    _check(lib().orc_pair_order_mode(n, M, _p(cell, C.c_int32), _p(idp, C.c_uint32), C.byref(params), step,
+                                     _p(cs, C.c_uint64), _p(order, C.c_uint32)))
+    return cs, order[:n]
+
+
 # ----------------------------------------------------------------------------- physics
-def make_params(cfg: dict, correction: bool = False) -> Params:
-    return Params(cfg["mass"], cfg["charge"], cfg["eps0"], cfg["weight"],
-                  cfg.get("n_neutral", 0.0), cfg.get("mass_neutral", 1.0),
-                  cfg.get("sigma_el", 0.0), cfg.get("sigma_ion", 0.0), cfg.get("e_ion", 1e30),
-                  int(cfg["seed"]), int(cfg.get("odd_mode", 0)), 1 if correction else 0)
+def make_params(cfg: dict, correction: bool = False, pairing_mode: int | None = None) -> Params:
+    """Oracle parameters of a workload; the pairing mode defaults to the workload's
+    ``pairing_mode`` (key sort when absent) and ``cell_ids`` (a subset's original cell
+    indices) address the per-cell random streams."""
+    mode = int(cfg.get("pairing_mode", PAIR_KEY) if pairing_mode is None else pairing_mode)
+    P = Params(cfg["mass"], cfg["charge"], cfg["eps0"], cfg["weight"],
+               cfg.get("n_neutral", 0.0), cfg.get("mass_neutral", 1.0),
+               cfg.get("sigma_el", 0.0), cfg.get("sigma_ion", 0.0), cfg.get("e_ion", 1e30),
+               int(cfg["seed"]), int(cfg.get("odd_mode", 0)), 1 if correction else 0, mode, 0, None)
+    cid = cfg.get("cell_ids")
+    if cid is not None:
+        P._cell_ids = np.ascontiguousarray(cid, dtype=np.uint32)    # kept alive with the struct
+        P.cell_ids = P._cell_ids.ctypes.data
+    return P
 
 
 def ta_pair(va, vb, A: float, words):

@@ -22,6 +22,11 @@
  *   orc_neutral         analytic collision counts, energy bookkeeping
  *   orc_moments         numpy bincount sums
  *   orc_nrl_lnlambda    hand-evaluated formulary values
+ *   orc_bij_*, orc_pair_order_mode (bijection mode)
+ *                       bijection and inverse on every tested size; chi^2
+ *                       uniformity of positions, partners and the left-out
+ *                       particle; rate of neighbouring-rank pairs; candidate
+ *                       count mean P_null N and uniform selection
  */
 #include <math.h>
 #include <stdint.h>
@@ -31,7 +36,13 @@
 #define ORC_PI 3.14159265358979323846
 
 /* Random-stream tags: which use a Philox block serves (counter word 2). */
-enum { ORC_TAG_PARTICLE = 1, ORC_TAG_PAIR = 2, ORC_TAG_SCATTER = 3, ORC_TAG_SECONDARY = 4 };
+enum { ORC_TAG_PARTICLE = 1, ORC_TAG_PAIR = 2, ORC_TAG_SCATTER = 3, ORC_TAG_SECONDARY = 4, ORC_TAG_PERM = 5 };
+
+/* Pairing modes (see orc_pair_order_ids).  In the bijection mode, cells of at
+ * least ORC_BIJ_MIN_N particles are paired through a keyed bijection of their
+ * id ranks; smaller cells keep the key sort. */
+enum { ORC_PAIR_KEY = 0, ORC_PAIR_BIJECTION = 1 };
+#define ORC_BIJ_MIN_N 4097u
 
 /* Error codes (same numeric meaning as the library's, defined independently). */
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ECAPACITY = -2 };
@@ -49,6 +60,9 @@ typedef struct {
     uint64_t seed;       /* Philox key                                   */
     int32_t odd_mode;    /* 0: last particle of an odd cell sits out     */
     int32_t correction;  /* 1: restore per-cell momentum+energy after TA */
+    int32_t pairing_mode;/* ORC_PAIR_KEY or ORC_PAIR_BIJECTION           */
+    int32_t reserved;
+    const uint32_t *cell_ids; /* random-stream id of each cell (NULL: its index) */
 } orc_params;
 
 /* ------------------------------------------------------------------------- *
@@ -181,6 +195,166 @@ int orc_pair_order_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t
 }
 
 /* ------------------------------------------------------------------------- *
+ * Pairing through a keyed bijection (the oracle's second pairing mode).
+ * Table 5 only asks that consecutive entries of a cell's index list be
+ * paired; any random perfect matching of the cell serves the Takizuka-Abe
+ * model.  Reading for cells of n >= ORC_BIJ_MIN_N particles: the cell's
+ * particles are ranked by ascending id (r = 0 .. n-1) and the particle of rank
+ * r takes pairing position pi(r), where pi is a bijection of [0, n) keyed by
+ * (seed, cell, step):
+ *   - the domain is written in mixed radix: a = ceil(sqrt(n)), b = ceil(n/a),
+ *     x = L b + R with L in [0, a), R in [0, b);
+ *   - six Feistel rounds alternate between the two radices: an even round maps
+ *     (L, R) with L in [0, a), R in [0, b) to (R, (L + F(R, K_i, a)) mod a) and
+ *     an odd round maps (L, R) with L in [0, b), R in [0, a) to
+ *     (R, (L + F(R, K_i, b)) mod b), so after six rounds L is in [0, a) again
+ *     and the image is L b + R in [0, a b);
+ *   - F(R, K, m) = floor(h m / 2^32), h = mix(R xor K), mix(t) = u * M2 mod
+ *     2^32 with u = w xor (w >> 16), w = t * M1 mod 2^32 (M1 = 0x9E3779B1,
+ *     M2 = 0x85EBCA6B);
+ *   - the round keys K_0..K_5 are words 0-3 of the Philox block with counter
+ *     (cell, step, PERM, 0) and words 0-1 of the block (cell, step, PERM, 1);
+ *     word 2 of the second block is the uniform that rounds the neutral step's
+ *     candidate count (orc_neutral_ids);
+ *   - images at or above n are mapped again (cycle walking), which restricts
+ *     the bijection of [0, a b) to one of [0, n).
+ * Pins: bijection and inverse for every tested n, uniformity of positions,
+ * partners and the left-out particle, and the rate of pairs of neighbouring
+ * ranks (tests/test_oracle_bijection.py).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t n, a, b;
+    uint32_t key[6];
+    uint32_t u;          /* candidate-count rounding word */
+} orc_bij;
+
+static uint32_t orc_bij_mix(uint32_t t)
+{
+    uint32_t w = t * 0x9E3779B1u;
+    uint32_t u = w ^ (w >> 16);
+    return u * 0x85EBCA6Bu;
+}
+
+static uint32_t orc_bij_f(uint32_t r, uint32_t key, uint32_t m)
+{
+    return (uint32_t)(((uint64_t)orc_bij_mix(r ^ key) * (uint64_t)m) >> 32);
+}
+
+void orc_bij_setup(uint64_t seed, uint64_t cell_id, uint32_t step, uint32_t n, orc_bij *B)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t c0[4] = {(uint32_t)cell_id, step, ORC_TAG_PERM, 0u};
+    uint32_t c1[4] = {(uint32_t)cell_id, step, ORC_TAG_PERM, 1u};
+    uint32_t w0[4], w1[4];
+    orc_philox4x32_10(c0, key, w0);
+    orc_philox4x32_10(c1, key, w1);
+    uint32_t a = 1;
+    while ((uint64_t)a * a < n) ++a;              /* ceil(sqrt(n)) */
+    B->n = n;
+    B->a = a;
+    B->b = n > 0 ? (n + a - 1) / a : 1;
+    for (int i = 0; i < 4; ++i) B->key[i] = w0[i];
+    B->key[4] = w1[0];
+    B->key[5] = w1[1];
+    B->u = w1[2];
+}
+
+/* One pass of the six rounds over [0, a b). */
+static uint32_t orc_bij_enc(const orc_bij *B, uint32_t x)
+{
+    uint32_t L = x / B->b, R = x % B->b;
+    for (int i = 0; i < 6; ++i) {
+        uint32_t m = (i % 2 == 0) ? B->a : B->b;
+        uint32_t t = (L + orc_bij_f(R, B->key[i], m)) % m;
+        L = R;
+        R = t;
+    }
+    return L * B->b + R;
+}
+
+/* Its inverse: the rounds undone in reverse order. */
+static uint32_t orc_bij_dec(const orc_bij *B, uint32_t y)
+{
+    uint32_t L = y / B->b, R = y % B->b;
+    for (int i = 5; i >= 0; --i) {
+        uint32_t m = (i % 2 == 0) ? B->a : B->b;
+        uint32_t prevR = L;
+        uint32_t prevL = (R + m - orc_bij_f(prevR, B->key[i], m)) % m;
+        L = prevL;
+        R = prevR;
+    }
+    return L * B->b + R;
+}
+
+uint32_t orc_bij_forward(const orc_bij *B, uint32_t r)
+{
+    uint32_t y = orc_bij_enc(B, r);
+    while (y >= B->n) y = orc_bij_enc(B, y);
+    return y;
+}
+
+uint32_t orc_bij_inverse(const orc_bij *B, uint32_t q)
+{
+    uint32_t x = orc_bij_dec(B, q);
+    while (x >= B->n) x = orc_bij_dec(B, x);
+    return x;
+}
+
+/* Test access: pi or its inverse for every element of [0, n). */
+int orc_bij_table(uint64_t seed, uint64_t cell_id, uint32_t step, uint32_t n, int inverse, uint32_t *out,
+                  uint32_t *params_out)
+{
+    orc_bij B;
+    orc_bij_setup(seed, cell_id, step, n, &B);
+    for (uint32_t k = 0; k < n; ++k) out[k] = inverse ? orc_bij_inverse(&B, k) : orc_bij_forward(&B, k);
+    if (params_out) {
+        params_out[0] = B.a; params_out[1] = B.b;
+        for (int i = 0; i < 6; ++i) params_out[2 + i] = B.key[i];
+        params_out[8] = B.u;
+    }
+    return ORC_OK;
+}
+
+static uint64_t orc_cell_id(const orc_params *p, int32_t j)
+{
+    return p->cell_ids ? (uint64_t)p->cell_ids[j] : (uint64_t)j;
+}
+
+typedef struct { uint32_t id; uint32_t l; } orc_il;
+
+static int orc_il_cmp(const void *a, const void *b)
+{
+    const orc_il *x = (const orc_il *)a, *y = (const orc_il *)b;
+    return x->id < y->id ? -1 : (x->id > y->id ? 1 : 0);
+}
+
+/* Pairing order of every cell under the mode in p: the key sort, or for
+ * cells of at least ORC_BIJ_MIN_N particles in the bijection mode, the
+ * particle of id rank r at position pi(r). */
+int orc_pair_order_mode(int64_t n, int32_t M, const int32_t *cell, const uint32_t *ids, const orc_params *p,
+                        uint32_t step, uint64_t *cell_start, uint32_t *order)
+{
+    int rc = orc_pair_order_ids(n, M, cell, ids, p->seed, step, cell_start, order);
+    if (rc || p->pairing_mode != ORC_PAIR_BIJECTION) return rc;
+    orc_il *tmp = (orc_il *)malloc(sizeof(orc_il) * (size_t)(n > 0 ? n : 1));
+    if (!tmp) return ORC_EINVAL;
+    for (int32_t j = 0; j < M; ++j) {
+        uint64_t s = cell_start[j], cnt = cell_start[j + 1] - cell_start[j];
+        if (cnt < ORC_BIJ_MIN_N) continue;
+        for (uint64_t k = 0; k < cnt; ++k) {
+            tmp[k].l = order[s + k];
+            tmp[k].id = (uint32_t)orc_id(ids, order[s + k]);
+        }
+        qsort(tmp, (size_t)cnt, sizeof(orc_il), orc_il_cmp);       /* ranks by ascending id */
+        orc_bij B;
+        orc_bij_setup(p->seed, orc_cell_id(p, j), step, (uint32_t)cnt, &B);
+        for (uint64_t r = 0; r < cnt; ++r) order[s + orc_bij_forward(&B, (uint32_t)r)] = tmp[r].l;
+    }
+    free(tmp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- *
  * Takizuka-Abe binary collision (Takizuka & Abe 1977, the model Sec. 4.4
  * adopts for step S1).  For a pair (a, b) of equal-mass electrons with
  * relative velocity u = v_a - v_b:
@@ -292,7 +466,7 @@ int orc_coulomb_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t *i
     uint64_t *cs = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1));
     uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     if (!cs || !order) { free(cs); free(order); return ORC_EINVAL; }
-    int rc = orc_pair_order_ids(n, M, cell, ids, p->seed, step, cs, order);
+    int rc = orc_pair_order_mode(n, M, cell, ids, p, step, cs, order);
     if (rc) { free(cs); free(order); return rc; }
     for (int32_t j = 0; j < M; ++j) {
         uint64_t s = cs[j], cnt = cs[j + 1] - cs[j];
@@ -332,7 +506,9 @@ int orc_coulomb_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t *i
  * with the null-collision method of Sec. 4.2 (Vahedi & Surendra 1995).
  * Per cell j: nu_max = n_n (sigma_el + sigma_ion) v_max with v_max the largest
  * speed in the cell at this point of the step, P_null = 1 - exp(-nu_max dt_j).
- * Particle l (PARTICLE block words 1, 2) is a candidate iff U1 < P_null; a
+ * Particle l (PARTICLE block words 1, 2) is a candidate iff U1 < P_null (in
+ * the bijection pairing mode, cells of at least ORC_BIJ_MIN_N particles take
+ * their candidates by pairing position instead, see below); a
  * candidate with r = U2 nu_max collides elastically if r < nu_el(v),
  * ionizes if r < nu_el(v) + nu_ion(v), and is otherwise a null collision.
  * Elastic: new direction uniform on the sphere (SCATTER words 0, 1), speed
@@ -343,7 +519,7 @@ int orc_coulomb_ids(int64_t n, int32_t M, const int32_t *cell, const uint32_t *i
  * and position.  Secondaries are appended (Table 3 CS5) at
  * N_old + offset(cell) + rank of the parent inside the cell, cells in
  * ascending order and parents in the cell's pairing order of this step
- * (sorted by (PARTICLE word 0, index)); reading: a deterministic form of the
+ * (orc_pair_order_mode); reading: a deterministic form of the
  * paper's atomic global write index.  Optional outputs: `decision` (0 not a
  * candidate, 1 null, 2 elastic, 3 ionization) and `margin` (distance of the
  * deciding uniform to the nearest decision boundary, relative to 1).
@@ -380,13 +556,54 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
     uint32_t *nion = (uint32_t *)calloc((size_t)M, sizeof(uint32_t));
     uint8_t *ionize = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
     double *sec = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    if (!vmax2 || !nion || !ionize || !sec) { free(vmax2); free(nion); free(ionize); free(sec); return ORC_EINVAL; }
+    /* bijection mode: candidates chosen by pairing position (see below) */
+    const int bij = p->pairing_mode == ORC_PAIR_BIJECTION;
+    int8_t *cand = bij ? (int8_t *)calloc((size_t)(n > 0 ? n : 1), 1) : NULL;
+    double *cmarg = bij ? (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1)) : NULL;
+    uint64_t *bcs = bij ? (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1)) : NULL;
+    uint32_t *bord = bij ? (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)) : NULL;
+    if (!vmax2 || !nion || !ionize || !sec || (bij && (!cand || !cmarg || !bcs || !bord))) {
+        free(vmax2); free(nion); free(ionize); free(sec); free(cand); free(cmarg); free(bcs); free(bord);
+        return ORC_EINVAL;
+    }
     for (int64_t l = 0; l < n; ++l) {
         double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
         if (v2 > vmax2[cell[l]]) vmax2[cell[l]] = v2;
     }
     const double sig_tot = p->sigma_el + p->sigma_ion;
     const double e_over_m = p->charge / p->mass;
+    /* Bijection mode, cells of at least ORC_BIJ_MIN_N particles: the paper
+     * selects P_null N particles at random (Sec. 4.2).  Reading: the count is
+     * n_c = floor(P_null N + U) with U the cell's candidate-count uniform
+     * (orc_bij_setup), so that its mean is P_null N, and the candidates are
+     * the particles at pairing positions 0 .. n_c - 1 of this step's order
+     * (a uniformly random subset, since the positions are a keyed bijection
+     * of the id ranks).  cmarg: distance of P_null N + U to the nearest
+     * integer relative to P_null N (for the two particles next to the cut). */
+    if (bij) {
+        int rc0 = orc_pair_order_mode(n, M, cell, ids, p, step, bcs, bord);
+        if (rc0) {
+            free(vmax2); free(nion); free(ionize); free(sec); free(cand); free(cmarg); free(bcs); free(bord);
+            return rc0;
+        }
+        for (int64_t l = 0; l < n; ++l) cmarg[l] = 1.0;
+        for (int32_t j = 0; j < M; ++j) {
+            uint64_t s0 = bcs[j], cnt = bcs[j + 1] - bcs[j];
+            if (cnt < ORC_BIJ_MIN_N) continue;
+            orc_bij B;
+            orc_bij_setup(p->seed, orc_cell_id(p, j), step, (uint32_t)cnt, &B);
+            double numax = p->n_neutral * sig_tot * sqrt(vmax2[j]);
+            double pnull = -expm1(-numax * dt[j]);
+            double t = pnull * (double)cnt + orc_uniform(B.u);
+            uint64_t nc = (uint64_t)floor(t);
+            if (nc > cnt) nc = cnt;
+            double fr = t - floor(t);
+            double cm = fmin(fr, 1.0 - fr) / fmax(pnull * (double)cnt, 1.0);
+            for (uint64_t q = 0; q < cnt; ++q) cand[bord[s0 + q]] = q < nc ? 1 : -1;
+            if (nc > 0) cmarg[bord[s0 + nc - 1]] = cm;
+            if (nc < cnt) cmarg[bord[s0 + nc]] = cm;
+        }
+    }
     int64_t ncand = 0, nel = 0, nio = 0;
     for (int64_t l = 0; l < n; ++l) {
         int32_t j = cell[l];
@@ -396,8 +613,15 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
         orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_PARTICLE, w);
         double uc = orc_uniform(w[1]);
         if (decision) decision[l] = 0;
-        if (margin) margin[l] = fabs(uc - pnull);
-        if (!(uc < pnull)) continue;
+        int is_cand;
+        if (bij && cand[l] != 0) {                 /* cell paired by the bijection */
+            is_cand = cand[l] > 0;
+            if (margin) margin[l] = cmarg[l];
+        } else {
+            is_cand = uc < pnull;
+            if (margin) margin[l] = fabs(uc - pnull);
+        }
+        if (!is_cand) continue;
         ++ncand;
         double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
         double v = sqrt(v2);
@@ -450,7 +674,7 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
         /* cells in ascending order; inside a cell, parents in pairing order */
         uint64_t *cs = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1));
         uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
-        if (!cs || !order || orc_pair_order_ids(n, M, cell, ids, p->seed, step, cs, order) != ORC_OK) {
+        if (!cs || !order || orc_pair_order_mode(n, M, cell, ids, p, step, cs, order) != ORC_OK) {
             rc = ORC_EINVAL;
         } else {
             int64_t dst = n;
@@ -467,7 +691,7 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
         free(cs); free(order);
     }
     if (counts_out) { counts_out[0] = ncand; counts_out[1] = nel; counts_out[2] = nio; }
-    free(vmax2); free(nion); free(ionize); free(sec);
+    free(vmax2); free(nion); free(ionize); free(sec); free(cand); free(cmarg); free(bcs); free(bord);
     return rc;
 }
 

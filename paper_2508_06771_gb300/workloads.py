@@ -228,6 +228,8 @@ def subset_cells(wl: dict, cells) -> dict:
     keep = remap[wl["cell"]] >= 0
     out = dict(wl)
     out["ids"] = np.nonzero(keep)[0].astype(np.uint32)    # original indices: the random-stream ids
+    base_ids = wl.get("cell_ids")
+    out["cell_ids"] = (cells if base_ids is None else np.asarray(base_ids)[cells]).astype(np.uint32)
     out.update(M=int(cells.size), vx=wl["vx"][keep], vy=wl["vy"][keep], vz=wl["vz"][keep],
                cell=remap[wl["cell"][keep]].astype(np.int32), inv_vol=wl["inv_vol"][cells],
                dt_cell=wl["dt_cell"][cells], lnlam_cell=wl["lnlam_cell"][cells])
