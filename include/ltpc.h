@@ -83,8 +83,26 @@ typedef struct ltpc_config {
                                    particle was loaded or appended since the
                                    last one (particles never change cells in
                                    this library); 0: group every step          */
-    int32_t reserved[7];        /* must be zero                                */
+    int32_t pairing_mode;       /* LTPC_PAIR_KEY (0) or LTPC_PAIR_BIJECTION    */
+    int32_t reserved[6];        /* must be zero                                */
 } ltpc_config;
+
+/* Pairing modes (Table 5 pairs consecutive entries of each cell's index list;
+ * the order is the library's reading, the same in every class of kernel).
+ *   LTPC_PAIR_KEY: every particle draws a key (word 0 of its PARTICLE Philox
+ *     block) and a cell's particles are ordered by (key, id); a particle is a
+ *     null-collision candidate when word 1 of that block gives U < P_null.
+ *   LTPC_PAIR_BIJECTION: cells of 4097..65536 particles put the particle of
+ *     id rank r (ascending ids) at pairing position pi(r), pi a keyed
+ *     bijection of [0, N_j) drawn per (seed, cell, step) (six mixed-radix
+ *     Feistel rounds with cycle walking); the null-collision candidates are
+ *     the particles at positions below floor(P_null N_j + U) (the paper's
+ *     "P_null N particles", Sec. 4.2).  Smaller cells are paired and sampled
+ *     as in LTPC_PAIR_KEY.  This mode needs storage grouped by cell (cell
+ *     ids never decreasing at load); a load that is not is rejected with
+ *     LTPC_EINVAL.  Particles appended by ionization keep the grouping. */
+#define LTPC_PAIR_KEY 0
+#define LTPC_PAIR_BIJECTION 1
 
 /* Bytes of the two caller-owned device buffers for `cfg`.
  * state_bytes: particle arrays (vx, vy, vz, cell, optional x) for
@@ -196,8 +214,9 @@ int ltpc_pair_order(ltpc_ctx* ctx, int64_t step, uint32_t* d_order, uint32_t* d_
 
 /* Inspection: the grouping of CCS1-CCS3 (cell_start[M+1], perm[n], counts[M];
  * device pointers, any may be NULL).  perm[cell_start[j] .. cell_start[j+1])
- * holds the ids of cell j: after a load ordered by cell, the loaded particles
- * first in index order, then appended ones; otherwise in unspecified order.
+ * holds the ids of cell j: the loaded particles (in index order after a load
+ * ordered by cell, otherwise in unspecified order), then the particles
+ * appended by ionization in index order.
  * Asynchronous. */
 int ltpc_grouping(ltpc_ctx* ctx, uint32_t* d_cell_start, uint32_t* d_perm, uint32_t* d_counts);
 

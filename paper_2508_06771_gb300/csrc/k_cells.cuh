@@ -28,6 +28,7 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include "bijection.cuh"
 #include "ltpc_index.h"
 #include "ltpc_internal.h"
 #include "philox.cuh"
@@ -585,6 +586,29 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const uint32_t k = tid + (uint32_t)i * NT;
             hl[i] = k < nh ? __ldcs(a.perm + s + hb + k) : 0u;
         }
+        // Bijection pairing (the cell's record says so; uniform over the cluster):
+        // the cell's index list is in ascending id order (storage grouped by cell),
+        // so home index hb + k is the particle's id rank and its pairing position
+        // is pi(hb + k) -- no keys, no sort.
+        const uint32_t* bw = reinterpret_cast<const uint32_t*>(a.cpar + (size_t)j * NCP + CP_BIJ);
+        const uint32_t bij_ab = __ldg(bw + CPB_AB);
+        uint32_t multi = 0u;           // items whose bucket holds several entries
+        if (bij_ab != 0u) {
+            BijParams B;
+            B.n = n; B.a = bij_ab & 0xFFFFu; B.b = bij_ab >> 16; B.mb = __ldg(bw + CPB_MB);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) B.key[q] = __ldg(bw + CPB_KEY + q);
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t k = tid + (uint32_t)i * NT;
+                hp[i] = k < nh ? bij_forward(B, hb + k) : 0u;
+            }
+            if (r == 0 && tid == 0) {   // the next work item, completed by the wait before phase 3
+                if (wnext < list_n) cp_async<16>(&s_item[par ^ 1u], a.list + wnext);
+                else s_item[par ^ 1u] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            pc.mark(1); pc.mark(2); pc.mark(3);
+        } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t k = tid + (uint32_t)i * NT;
@@ -665,7 +689,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         pc.mark(2);
         // ---- 1d. place (key, id) at bucket start + slot, in the position-owner CTA.
         // SB: a particle alone in its bucket has its final position already.
-        uint32_t multi = 0u;           // items whose bucket holds several entries
         if constexpr (SB) {
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
@@ -768,6 +791,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             }
         }
         Cl<C>::sync();
+        }   // key sort
 
         pc.mark(4);
         pc.mark(5);
@@ -994,11 +1018,21 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             }
             const T nsel = a.c_nsig_el, nsion = a.c_nsig_ion;
             const T e_ion = a.c_e_ion, mr2 = a.c_mratio2;
+            // Bijection pairing: the candidates are the particles at pairing positions
+            // below n_c = floor(P_null N + U) (binary64 products without contraction,
+            // as the reference computes them); otherwise each particle's own uniform
+            // decides (U < P_null, its 16 top bits screened by hmin first).
+            uint32_t n_cand = 0u;
+            if (bij_ab != 0u) {
+                const double t = __dadd_rn(__dmul_rn((double)pnull, (double)n), unif<double>(__ldg(bw + CPB_U)));
+                const double f = floor(t);
+                n_cand = f <= 0.0 ? 0u : (f >= (double)n ? n : (uint32_t)f);
+            }
             bool ionized = false;
             auto collide = [&](uint32_t q) {
                 const uint32_t l = sl[q];
                 const uint4 rw = draw(a.keys, l, step, TAG_PARTICLE);
-                if (!(unif<T>(rw.y) < pnull)) return;
+                if (bij_ab == 0u && !(unif<T>(rw.y) < pnull)) return;
                 const T x = svx[q], y = svy[q], z = svz[q];
                 const T v2 = x * x + y * y + z * z;
                 const T v = Math<T>::sqrt(v2);
@@ -1021,7 +1055,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             // candidate bit mask over local positions, then block-wide compaction
             for (uint32_t q0 = 0; q0 < nloc; q0 += NT) {
                 const uint32_t q = q0 + tid;
-                const bool maybe = q < nloc && (uint32_t)sw[q] < hmin;
+                const bool maybe = q < nloc && (bij_ab != 0u ? pb + q < n_cand : (uint32_t)sw[q] < hmin);
                 const unsigned m = __ballot_sync(0xFFFFFFFFu, maybe);
                 if ((tid & 31u) == 0u && q0 + tid < nloc + 31u) s_cmask[(q0 + tid) >> 5] = m;
             }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bijection.cuh"
 #include "ltpc_internal.h"
 #include "ltpc_launch.h"
 
@@ -43,8 +44,13 @@ static __global__ void k_hist(const int32_t* __restrict__ cell, uint32_t* __rest
 //     pass starts from when their count equals N_j; otherwise (an append rolled
 //     back by a capacity error), or when the cell drifts faster than its thermal
 //     speed (cancellation in the uncentred sums), K0 = -1 asks the pass to form
-//     centred sums itself.
-__device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
+//     centred sums itself;
+//   * in the bijection pairing mode, for a cell of BIJ_MIN_N..BIJ_MAX_N
+//     particles, the shape (a, b), the six round keys and the candidate-count
+//     word of its pairing bijection (bijection.cuh): words 0-3 of the Philox
+//     block (cell, step, PERM, 0), then words 0-2 of the block (cell, step,
+//     PERM, 1).
+__device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt, uint32_t step)
 {
     // One binary64 division per cell (1 / sum of counts of the stored moments);
     // everything else is products, since binary64 runs on a narrow pipe here.
@@ -97,6 +103,19 @@ __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
     f[5] = (float)K0;
     f[6] = (float)o[CP_INVN];
     f[7] = 0.0f;
+    uint32_t* w = reinterpret_cast<uint32_t*>(o + CP_BIJ);
+    for (int q = 0; q < CPB_WORDS; ++q) w[q] = 0u;
+    if (cp.bijection && n >= BIJ_MIN_N && n <= BIJ_MAX_N) {
+        uint32_t a, b, mb;
+        bij_shape(n, &a, &b, &mb);
+        const uint4 w0 = philox4x32_10((uint32_t)j, step, TAG_PERM, 0u, cp.keys);
+        const uint4 w1 = philox4x32_10((uint32_t)j, step, TAG_PERM, 1u, cp.keys);
+        w[CPB_AB] = a | (b << 16);
+        w[CPB_MB] = mb;
+        w[CPB_KEY + 0] = w0.x; w[CPB_KEY + 1] = w0.y; w[CPB_KEY + 2] = w0.z; w[CPB_KEY + 3] = w0.w;
+        w[CPB_KEY + 4] = w1.x; w[CPB_KEY + 5] = w1.y;
+        w[CPB_U] = w1.z;
+    }
 }
 
 // CCS3: perm[I_j + rank] = l.  Cell ids outside [0, M) are skipped (the load's
@@ -109,16 +128,19 @@ __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt)
 // per-cell scalars of the pass (cell_params above), one thread per cell.
 static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __restrict__ cell, int32_t M, uint32_t* __restrict__ cursor,
                                  uint32_t* __restrict__ perm, const DevState* __restrict__ ds, CellParamArgs cp,
-                                 const uint32_t* __restrict__ run_start, const uint32_t* __restrict__ cell_start)
+                                 const uint32_t* __restrict__ run_start, const uint32_t* __restrict__ cell_start,
+                                 const uint32_t* __restrict__ aslot)
 {
     if (cp.cpar) {                                   // this pass's per-cell scalars, one thread per cell
         const double dt = ds->dt;
+        const uint32_t step = ds->step;
         for (int32_t j = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); j < M; j += (int32_t)(gridDim.x * blockDim.x))
-            cell_params(cp, j, dt);
+            cell_params(cp, j, dt, step);
     }
     if (ds->grouping_valid) return;                  // cached grouping: perm is current
     const unsigned long long n = ds->n;
     const unsigned long long n_sorted = ds->n_sorted;   // particles below lie in their cell's run
+    const unsigned long long n_loaded = ds->n_loaded;   // particles from here on were appended (slot known)
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long w0 = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -138,13 +160,19 @@ static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __rest
         const bool same = c[0] == c0 && c[1] == c0 && c[2] == c0 && c[3] == c0;
         if (__all_sync(0xFFFFFFFFu, same) && c0 >= 0) {           // one cell, 128 particles
             uint32_t b = 0u;
+            const uint32_t l = (uint32_t)l0;
+            if (base >= n_loaded) {                               // appended: each at its recorded slot
+                const uint32_t cs = cell_start[c0];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) perm[cs + aslot[l + u]] = l + (uint32_t)u;
+                continue;
+            }
             if (base + 128ull <= n_sorted) {                      // in the cell's run: no atomic
                 b = cell_start[c0] + (uint32_t)(base - run_start[c0]) + 4u * lane;
             } else {
                 if (lane == 0) b = atomicAdd(&cursor[c0], 128u);
                 b = __shfl_sync(0xFFFFFFFFu, b, 0) + 4u * lane;
             }
-            const uint32_t l = (uint32_t)l0;
             if ((b & 3u) == 0u) {
                 *reinterpret_cast<uint4*>(perm + b) = make_uint4(l, l + 1u, l + 2u, l + 3u);
             } else {
@@ -158,6 +186,9 @@ static __global__ void __launch_bounds__(256, 8) k_scatter(const int32_t* __rest
             int32_t ca = c[u];
             if (ca >= 0 && l < n_sorted) {                        // in its cell's run
                 perm[cell_start[ca] + (uint32_t)(l - run_start[ca])] = (uint32_t)l;
+                ca = -1;
+            } else if (ca >= 0 && l >= n_loaded) {                // appended: at its recorded slot
+                perm[cell_start[ca] + aslot[l]] = (uint32_t)l;
                 ca = -1;
             }
             const unsigned peers = __match_any_sync(0xFFFFFFFFu, ca);
@@ -324,13 +355,15 @@ k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_
 
 // Copy the secondaries staged by the last pass to the end of the particle
 // arrays: secondary g (in cell order, then pairing-order position of the
-// parent) goes to slot n_old + g with the parent's cell and position.
+// parent) goes to slot n_old + g with the parent's cell and position, and
+// records its place in the cell's grouping: the cell's count before this
+// append (from the previous offsets) plus its rank among the cell's new ones.
 template <class T>
 static __global__ void k_append(int32_t M, const uint32_t* __restrict__ ion_off, const uint32_t* __restrict__ cs_prev,
                          const uint32_t* __restrict__ stage_l, const T* __restrict__ svx,
                          const T* __restrict__ svy, const T* __restrict__ svz, T* __restrict__ vx,
                          T* __restrict__ vy, T* __restrict__ vz, int32_t* __restrict__ cell,
-                         T* __restrict__ x, const DevState* __restrict__ ds)
+                         T* __restrict__ x, uint32_t* __restrict__ aslot, const DevState* __restrict__ ds)
 {
     const uint32_t tot = ds->n_ion;
     if (tot == 0u) return;
@@ -347,6 +380,7 @@ static __global__ void k_append(int32_t M, const uint32_t* __restrict__ ion_off,
         const uint32_t parent = stage_l[src];
         vx[dst] = svx[src]; vy[dst] = svy[src]; vz[dst] = svz[src];
         cell[dst] = lo;
+        aslot[dst] = (cs_prev[lo + 1] - cs_prev[lo]) + (g - ion_off[lo]);
         if (x) x[dst] = x[parent];
     }
 }
@@ -369,10 +403,12 @@ static __global__ void k_runs_check(const int32_t* __restrict__ cell, int32_t M,
 }
 
 static __global__ void k_runs_set(const int32_t* __restrict__ cell, int32_t M, const uint32_t* __restrict__ counts,
-                                  uint32_t* __restrict__ run_start, uint32_t* __restrict__ run_len, DevState* ds)
+                                  uint32_t* __restrict__ run_start, uint32_t* __restrict__ run_len, DevState* ds,
+                                  int require_grouped)
 {
     const unsigned long long n = ds->n;
     const bool grouped = ds->load_unsorted == 0u;
+    if (require_grouped && !grouped && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ds->err, ERR_UNGROUPED);
     const unsigned long long gt = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long c = gt; c < (unsigned long long)M; c += stride) run_len[c] = grouped ? counts[c] : 0u;
@@ -394,7 +430,10 @@ static __global__ void k_reset_cursors(int32_t M, const uint32_t* __restrict__ c
 
 static __global__ void k_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step)
 {
-    if (set_n) { ds->n = n; ds->n_ion = 0u; ds->grouping_valid = 0u; ds->load_unsorted = 0u; ds->n_sorted = 0ull; }
+    if (set_n) {
+        ds->n = n; ds->n_ion = 0u; ds->grouping_valid = 0u; ds->load_unsorted = 0u; ds->n_sorted = 0ull;
+        ds->n_loaded = n;
+    }
     if (set_step) { ds->step = step; ds->dt = dt; }
 }
 
@@ -423,7 +462,8 @@ cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uin
                            const CellParamArgs* cp)
 {
     CellParamArgs none = {};
-    k_scatter<<<grid, 256, 0, s>>>(cell, M, cursor, perm, ds, cp ? *cp : none, runs.run_start, cell_start);
+    k_scatter<<<grid, 256, 0, s>>>(cell, M, cursor, perm, ds, cp ? *cp : none, runs.run_start, cell_start,
+                                   runs.aslot);
     return cudaGetLastError();
 }
 
@@ -439,23 +479,23 @@ cudaError_t launch_regroup(int32_t M, uint32_t* counts, uint32_t* cell_start, ui
 template <class T>
 cudaError_t launch_append(int32_t M, const uint32_t* ion_off, const uint32_t* cs_prev, const uint32_t* stage_l,
                           const T* svx, const T* svy, const T* svz, T* vx, T* vy, T* vz, int32_t* cell, T* x,
-                          const DevState* ds, int grid, cudaStream_t s)
+                          uint32_t* aslot, const DevState* ds, int grid, cudaStream_t s)
 {
-    k_append<T><<<grid, 256, 0, s>>>(M, ion_off, cs_prev, stage_l, svx, svy, svz, vx, vy, vz, cell, x, ds);
+    k_append<T><<<grid, 256, 0, s>>>(M, ion_off, cs_prev, stage_l, svx, svy, svz, vx, vy, vz, cell, x, aslot, ds);
     return cudaGetLastError();
 }
 template cudaError_t launch_append<float>(int32_t, const uint32_t*, const uint32_t*, const uint32_t*, const float*,
                                           const float*, const float*, float*, float*, float*, int32_t*, float*,
-                                          const DevState*, int, cudaStream_t);
+                                          uint32_t*, const DevState*, int, cudaStream_t);
 template cudaError_t launch_append<double>(int32_t, const uint32_t*, const uint32_t*, const uint32_t*,
                                            const double*, const double*, const double*, double*, double*, double*,
-                                           int32_t*, double*, const DevState*, int, cudaStream_t);
+                                           int32_t*, double*, uint32_t*, const DevState*, int, cudaStream_t);
 
 cudaError_t launch_runs(const int32_t* cell, int32_t M, const uint32_t* counts, const RegroupLists& runs, DevState* ds,
-                        int grid, cudaStream_t s)
+                        int grid, cudaStream_t s, int require_grouped)
 {
     k_runs_check<<<grid, 256, 0, s>>>(cell, M, ds);
-    k_runs_set<<<grid, 256, 0, s>>>(cell, M, counts, runs.run_start, runs.run_len, ds);
+    k_runs_set<<<grid, 256, 0, s>>>(cell, M, counts, runs.run_start, runs.run_len, ds, require_grouped);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ struct Layout {
     size_t vx, vy, vz, cell, x;
     // work offsets
     size_t perm, counts, cell_start, cs_prev, cursor, ion_count, ion_off, stage_l, stage_vx, stage_vy,
-        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, lists, ds;
+        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, lists, ds;
 };
 
 bool compute_layout(const ltpc_config* c, Layout* L)
@@ -68,6 +68,7 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->cpar = take(M * NCP * 8);
     L->run_start = take(M * 4);
     L->run_len = take(M * 4);
+    L->aslot = take(cap * 4);
     L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
     L->work = o;
@@ -132,6 +133,7 @@ int set_table(ltpc_ctx* ctx, int table)
     ctx->lists.cache_grouping = ctx->cfg.cache_grouping;
     ctx->lists.run_start = ctx->w<uint32_t>(ctx->L.run_start);
     ctx->lists.run_len = ctx->w<uint32_t>(ctx->L.run_len);
+    ctx->lists.aslot = ctx->w<uint32_t>(ctx->L.aslot);
     for (int k = 0; k < MAX_CLASSES; ++k) {
         ctx->lists.max_n[k] = 0;
         ctx->lists.list[k] = ctx->w<uint4>(ctx->L.lists) + (size_t)k * ctx->cfg.n_cells;
@@ -214,6 +216,8 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
     cp.weight = ctx->cfg.weight;
     cp.e_over_m = ctx->cfg.charge / ctx->cfg.mass;
     cp.lnl_nrl = ctx->cfg.lnlambda_mode == LTPC_LNL_NRL ? 1 : 0;
+    cp.bijection = ctx->cfg.pairing_mode == LTPC_PAIR_BIJECTION ? 1 : 0;
+    cp.keys = philox_keys(ctx->cfg.seed);
     CK(launch_scatter(ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
                       grid_stream, s, ctx->lists, ctx->w<uint32_t>(L.cell_start), &cp));
     CK(mark());
@@ -236,8 +240,8 @@ int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
     CK(launch_append<T>(ctx->cfg.n_cells, ctx->w<uint32_t>(L.ion_off), ctx->w<uint32_t>(L.cs_prev),
                         ctx->w<uint32_t>(L.stage_l), ctx->w<T>(L.stage_vx), ctx->w<T>(L.stage_vy),
                         ctx->w<T>(L.stage_vz), ctx->s<T>(L.vx), ctx->s<T>(L.vy), ctx->s<T>(L.vz),
-                        ctx->s<int32_t>(L.cell), ctx->cfg.has_position ? ctx->s<T>(L.x) : nullptr, ctx->ds,
-                        ctx->sms * 2, s));
+                        ctx->s<int32_t>(L.cell), ctx->cfg.has_position ? ctx->s<T>(L.x) : nullptr,
+                        ctx->w<uint32_t>(L.aslot), ctx->ds, ctx->sms * 2, s));
     CK(mark());
     return LTPC_OK;
 }
@@ -285,7 +289,7 @@ int map_err_bits(uint32_t bits)
     if (bits & ERR_INDEX) return LTPC_EINTERNAL;
     if (bits & ERR_CAPACITY) return LTPC_ECAPACITY;
     if (bits & ERR_NONFINITE) return LTPC_ENONFINITE;
-    if (bits & ERR_BAD_CELL) return LTPC_EINVAL;
+    if (bits & (ERR_BAD_CELL | ERR_UNGROUPED)) return LTPC_EINVAL;
     if (bits & ERR_CELL_TOO_LARGE) return LTPC_EUNSUPPORTED;
     if (bits & ERR_TIMEOUT) return LTPC_ETIMEOUT;
     return LTPC_OK;
@@ -363,7 +367,8 @@ int ltpc_create(ltpc_ctx** out, const ltpc_config* cfg, void* d_state, void* d_w
         return LTPC_EINVAL;
     if (cfg->lnlambda_mode != LTPC_LNL_CONST && cfg->lnlambda_mode != LTPC_LNL_NRL) return LTPC_EINVAL;
     if (cfg->cache_grouping != 0 && cfg->cache_grouping != 1) return LTPC_EINVAL;
-    for (int i = 0; i < 7; ++i)
+    if (cfg->pairing_mode != LTPC_PAIR_KEY && cfg->pairing_mode != LTPC_PAIR_BIJECTION) return LTPC_EINVAL;
+    for (int i = 0; i < 6; ++i)
         if (cfg->reserved[i]) return LTPC_EINVAL;
     ltpc_ctx* ctx = new (std::nothrow) ltpc_ctx();
     if (!ctx) return LTPC_EINVAL;
@@ -445,7 +450,7 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
     int rc = async ? LTPC_OK : read_errors(ctx);
     if (rc) return rc;
     CK(launch_runs(ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(L.counts), ctx->lists, ctx->ds,
-                   ctx->sms * 8, s));
+                   ctx->sms * 8, s, ctx->cfg.pairing_mode == LTPC_PAIR_BIJECTION ? 1 : 0));
     CK(launch_regroup(ctx->cfg.n_cells, ctx->w<uint32_t>(L.counts), ctx->w<uint32_t>(L.cell_start),
                       ctx->w<uint32_t>(L.cs_prev), ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.ion_count),
                       ctx->w<uint32_t>(L.ion_off), ctx->lists, (unsigned long long)ctx->cfg.capacity, 0, 0, ctx->ds,

@@ -15,6 +15,7 @@ enum : uint32_t {
     ERR_INDEX = 8u,          // an internal index failed its bounds check (bug guard)
     ERR_CELL_TOO_LARGE = 16u,// a cell exceeds the largest cluster class
     ERR_BAD_CELL = 32u,      // a loaded cell id is outside [0, M)
+    ERR_UNGROUPED = 64u,     // the bijection pairing mode was given storage not grouped by cell
 };
 
 // What one pass of the cell kernel does.
@@ -43,6 +44,8 @@ struct DevState {
     unsigned int grouping_valid;      // 1: perm still groups the particles (no load, no append since)
     unsigned int load_unsorted;       // 1: the loaded storage is not grouped by cell
     unsigned long long n_sorted;      // particles [0, n_sorted) lie in per-cell runs (cell-grouped load)
+    unsigned long long n_loaded;      // particles [n_loaded, n) were appended: each has its slot in its
+                                      // cell's grouping (RegroupLists::aslot)
 };
 
 // Per-cell scalars of one pass, formed by a grid-wide loop at the start of
@@ -57,7 +60,17 @@ enum : int {
     CP_INVN = 6,     // 1 / N_j
     CP_LNL = 7,      // Coulomb logarithm used
     CP_F32 = 8,      // 8..11: binary32 copies of A, dt, the mean velocity, K0 and 1 / N_j (seven floats)
-    NCP = 12
+    CP_BIJ = 12,     // 12..16: the bijection pairing of the cell as ten 32-bit words (CPB_*), all zero
+                     // when the cell is paired by the key sort
+    NCP = 18
+};
+// Words of the bijection record (bijection.cuh).
+enum : int {
+    CPB_AB = 0,      // a | b << 16 (0: key sort)
+    CPB_MB = 1,      // ceil(2^32 / b)
+    CPB_KEY = 2,     // 2..7: the six round keys
+    CPB_U = 8,       // candidate-count rounding word
+    CPB_WORDS = 10
 };
 struct CellParamArgs {
     const uint32_t* counts;      // N_j of this pass
@@ -68,6 +81,8 @@ struct CellParamArgs {
     double* cpar;                // [M][NCP] out; nullptr: not formed
     double coef0, weight, e_over_m;
     int lnl_nrl;                 // 1: Coulomb logarithm by the NRL e-e formula
+    int bijection;               // 1: cells of BIJ_MIN_N..BIJ_MAX_N particles are paired by the bijection
+    PhiloxKeys keys;             // round keys of the seed (the bijection's round keys are drawn per cell)
 };
 
 // Arguments of the cell kernel (one cluster per cell).

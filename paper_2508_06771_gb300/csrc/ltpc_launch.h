@@ -21,6 +21,11 @@ struct RegroupLists {
     // grouping in index order; appended particles follow.
     uint32_t* run_start;
     uint32_t* run_len;
+    // Slot of every appended particle in its cell's grouping: the cell's
+    // count before the append plus the particle's rank among that pass's
+    // secondaries of the cell.  The scatter places appended particles there
+    // without atomics, after the loaded ones, in ascending index order.
+    uint32_t* aslot;
 };
 
 // One compiled shape of the cell kernel.
@@ -60,7 +65,7 @@ cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uin
                            cudaStream_t s, const RegroupLists& runs, const uint32_t* cell_start,
                            const CellParamArgs* cp = nullptr);
 cudaError_t launch_runs(const int32_t* cell, int32_t M, const uint32_t* counts, const RegroupLists& runs, DevState* ds,
-                        int grid, cudaStream_t s);
+                        int grid, cudaStream_t s, int require_grouped);
 cudaError_t launch_reset_cursors(int32_t M, const uint32_t* cell_start, const RegroupLists& runs, uint32_t* cursor,
                                  cudaStream_t s);
 cudaError_t launch_regroup(int32_t M, uint32_t* counts, uint32_t* cell_start, uint32_t* cs_prev, uint32_t* cursor,
@@ -69,7 +74,7 @@ cudaError_t launch_regroup(int32_t M, uint32_t* counts, uint32_t* cell_start, ui
 template <class T>
 cudaError_t launch_append(int32_t M, const uint32_t* ion_off, const uint32_t* cs_prev, const uint32_t* stage_l,
                           const T* svx, const T* svy, const T* svz, T* vx, T* vy, T* vz, int32_t* cell, T* x,
-                          const DevState* ds, int grid, cudaStream_t s);
+                          uint32_t* aslot, const DevState* ds, int grid, cudaStream_t s);
 cudaError_t launch_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step,
                              cudaStream_t s);
 template <class T>

@@ -20,6 +20,7 @@ OK, EINVAL, ECAPACITY, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EINTERNAL = 0,
 F32, F64 = 0, 1
 LOAD_SRC_DEVICE, LOAD_ASYNC = 1, 2   # flags of ltpc_load_particles
 LNL_CONST, LNL_NRL = 0, 1
+PAIR_KEY, PAIR_BIJECTION = 0, 1      # ltpc_config.pairing_mode
 
 _lock = threading.Lock()
 _lib = None
@@ -43,7 +44,8 @@ class Config(C.Structure):
         ("lnlambda_mode", C.c_int32), ("correction", C.c_int32), ("has_position", C.c_int32),
         ("use_graph", C.c_int32),
         ("inv_volume", C.POINTER(C.c_double)), ("dt_factor", C.POINTER(C.c_double)),
-        ("lnlambda", C.POINTER(C.c_double)), ("cache_grouping", C.c_int32), ("reserved", C.c_int32 * 7),
+        ("lnlambda", C.POINTER(C.c_double)), ("cache_grouping", C.c_int32), ("pairing_mode", C.c_int32),
+        ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -124,7 +126,7 @@ class Collider:
                  mass_neutral: float = 1.0, sigma_el: float = 0.0, sigma_ion: float = 0.0, e_ion: float = 1e30,
                  lnlambda_mode: int = LNL_CONST, correction: int = -1, has_position: bool = False,
                  use_graph: bool = True, dt_factor=None, lnlambda=None, device=None, stream=None,
-                 cache_grouping: bool = False):
+                 cache_grouping: bool = False, pairing_mode: int = PAIR_KEY):
         import torch
 
         self.torch = torch
@@ -149,6 +151,8 @@ class Collider:
         cfg.lnlambda_mode, cfg.correction = lnlambda_mode, correction
         cfg.has_position, cfg.use_graph = int(bool(has_position)), int(bool(use_graph))
         cfg.cache_grouping = int(bool(cache_grouping))
+        cfg.pairing_mode = int(pairing_mode)
+        self.pairing_mode = int(pairing_mode)
         cfg.inv_volume = _f64p(self._inv)
         cfg.dt_factor = _f64p(self._dtf) if self._dtf is not None else None
         cfg.lnlambda = _f64p(self._lnl) if self._lnl is not None else None
@@ -175,6 +179,7 @@ class Collider:
                 weight=wl["weight"], n_neutral=wl["n_neutral"] if wl.get("neutral", True) else 0.0,
                 mass_neutral=wl["mass_neutral"], sigma_el=wl["sigma_el"], sigma_ion=wl["sigma_ion"],
                 e_ion=wl["e_ion"], lnlambda_mode=wl.get("lnlam_mode", 0), correction=correction,
+                pairing_mode=kw.pop("pairing_mode", wl.get("pairing_mode", PAIR_KEY)),
                 has_position=wl.get("x") is not None, use_graph=use_graph,
                 dt_factor=np.asarray(wl["dt_cell"]) / dt, lnlambda=wl["lnlam_cell"], **kw)
         c.dt = dt

@@ -104,6 +104,8 @@ def test_grouping_after_appends(L, orc, shuffled):
     for j in range(wl["M"]):
         a, b = int(ocs[j]), int(ocs[j + 1])
         assert np.array_equal(np.sort(perm[a:b]), operm[a:b]), j
+    if not shuffled:   # cell-ordered load: loaded ids in index order, then the appended ones at their slots
+        assert np.array_equal(perm, operm)
     gcs, gorder = col.pair_order(3)
     ocs2, oorder = orc.pair_order(cell, wl["M"], wl["seed"], 3)
     assert np.array_equal(gorder, oorder)
