@@ -300,6 +300,8 @@ def run_ours(args, rank, world, local_rank):
     B.build()
     wl, desc = make_workload(args.workload, seed=rank, cells=args.cells)
     prec = "f32" if wl["precision"] == "f32" else "f64"
+    pmode = ltpc.PAIR_BIJECTION if args.pairing == "bijection" else ltpc.PAIR_KEY
+    wl["pairing_mode"] = pmode
     col = ltpc.Collider.from_workload(wl, precision=ltpc.F32 if prec == "f32" else ltpc.F64)
     dt = col.dt
     col.load_workload(wl)
@@ -319,6 +321,7 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         SG.identity_norm(net)
         wl_tr, _ = make_workload(args.workload, seed=1000 + rank, cells=args.cells)
+        wl_tr["pairing_mode"] = pmode
         col_tr = ltpc.Collider.from_workload(wl_tr)
         col_tr.load_workload(wl_tr)
         X, T, _ = SG.collect(col_tr, net, dt, 0, args.train_steps, every=args.train_every,
@@ -543,6 +546,7 @@ def run_ours(args, rank, world, local_rank):
                            n0 * (16 if prec == 'f32' else 28) / 1e6),
                        "class_table": [f"C={c['cluster']} x {c['threads']} thr, cells<={c['max_n']}" for c in classes],
                        "class_table_index": table, "autotuned": not args.no_autotune,
+                       "pairing": args.pairing,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": names[dom],
@@ -570,6 +574,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tail_4096x10000", choices=["relax_64x1000", "tail_4096x10000", "loguniform_256x256", "instances_64"])
     ap.add_argument("--no-autotune", action="store_true", help="keep the default class table")
+    ap.add_argument("--pairing", default="key", choices=["key", "bijection"],
+                    help="in-cell pairing: key sort, or the keyed bijection for cells above 4096")
     ap.add_argument("--cells", type=int, default=None, help="tail_4096x10000 only: number of cells (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

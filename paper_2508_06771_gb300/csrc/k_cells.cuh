@@ -403,6 +403,23 @@ template <> __device__ __forceinline__ uint32_t cand_threshold<double>(double pn
     return h <= 0.0 ? 0u : h >= 65536.0 ? 65536u : (uint32_t)h;
 }
 
+// Null-collision candidate count of the bijection pairing mode,
+// floor(P_null N + U) with U = (w + 1/2) 2^-32 clamped to [0, N].  binary64
+// takes the reference's products without contraction; binary32 stays off the
+// narrow binary64 pipe (its count can differ from the binary64 one only when
+// P_null N + U lies within a few binary32 ulps of an integer).
+template <class T> __device__ __forceinline__ uint32_t cand_count(T pnull, uint32_t n, uint32_t w);
+template <> __device__ __forceinline__ uint32_t cand_count<double>(double pnull, uint32_t n, uint32_t w)
+{
+    const double f = floor(__dadd_rn(__dmul_rn(pnull, (double)n), unif<double>(w)));
+    return f <= 0.0 ? 0u : (f >= (double)n ? n : (uint32_t)f);
+}
+template <> __device__ __forceinline__ uint32_t cand_count<float>(float pnull, uint32_t n, uint32_t w)
+{
+    const float f = floorf(fmaf(pnull, (float)n, unif<float>(w)));
+    return f <= 0.0f ? 0u : (f >= (float)n ? n : (uint32_t)f);
+}
+
 // Begins of the C ranges of a split (ltpc_index.h), kept in registers so that
 // the owner of an item is found by C-1 compares instead of a division.
 template <int C>
@@ -863,7 +880,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             // formed here instead)
             const T A = cell_scalar<T>(s_cp, 0), cx = cell_scalar<T>(s_cp, 2), cy = cell_scalar<T>(s_cp, 3),
                     cz = cell_scalar<T>(s_cp, 4);
-            const bool pre_mom = s_cp[CP_K0] >= 0.0;  // uniform over the cluster (same scalars)
+            const bool pre_mom = cell_scalar<T>(s_cp, 5) >= T(0);  // uniform over the cluster (same scalars)
             // Pair slot p holds positions 2p and 2p+1, so the pair's two particles sit
             // in the two lanes of one packed value: the update v_a += Du/2, v_b -= Du/2
             // and the sums are packed operations.  The restoration and the moments
@@ -1019,15 +1036,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const T nsel = a.c_nsig_el, nsion = a.c_nsig_ion;
             const T e_ion = a.c_e_ion, mr2 = a.c_mratio2;
             // Bijection pairing: the candidates are the particles at pairing positions
-            // below n_c = floor(P_null N + U) (binary64 products without contraction,
-            // as the reference computes them); otherwise each particle's own uniform
-            // decides (U < P_null, its 16 top bits screened by hmin first).
-            uint32_t n_cand = 0u;
-            if (bij_ab != 0u) {
-                const double t = __dadd_rn(__dmul_rn((double)pnull, (double)n), unif<double>(__ldg(bw + CPB_U)));
-                const double f = floor(t);
-                n_cand = f <= 0.0 ? 0u : (f >= (double)n ? n : (uint32_t)f);
-            }
+            // below n_c = floor(P_null N + U) (cand_count); otherwise each particle's own
+            // uniform decides (U < P_null, its 16 top bits screened by hmin first).
+            const uint32_t n_cand = bij_ab != 0u ? cand_count<T>(pnull, n, __ldg(bw + CPB_U)) : 0u;
             bool ionized = false;
             auto collide = [&](uint32_t q) {
                 const uint32_t l = sl[q];

@@ -15,6 +15,7 @@ static const CellKernelEntry kF32[] = {
     CellKernel<float, 1, 512, 24>::entry(),   // 7: <= 12288, one 512-thread CTA per cell
     CellKernel<float, 2, 1024, 12>::entry(),  // 8: <= 24576, clusters of two 1024-thread CTAs
     CellKernel<float, 4, 1024, 12>::entry(),  // 9: <= 49152, clusters of four 1024-thread CTAs
+    HomeKernel<float, 1024, 12288>::entry(),  // 10: bijection cells <= 12288, home order, bulk copies
 };
 
 int cell_kernels_f32(const CellKernelEntry** out)

@@ -13,6 +13,7 @@ static const CellKernelEntry kF64[] = {
     CellKernel<double, 1, 512, 8>::entry(),   // 5: <= 4096
     CellKernel<double, 1, 1024, 6>::entry(),  // 6: <= 6144, one CTA per cell
     CellKernel<double, 2, 1024, 6>::entry(),  // 7: <= 12288
+    HomeKernel<double, 1024, 6144>::entry(),  // 8: bijection cells <= 6144, home order, bulk copies
 };
 
 int cell_kernels_f64(const CellKernelEntry** out)

@@ -1,6 +1,7 @@
 // k_cells_inst.cuh -- launch wrapper for one compiled shape of the cell kernel.
 #pragma once
 #include "k_cells.cuh"
+#include "k_home.cuh"
 #include "ltpc_launch.h"
 
 namespace ltpc {
@@ -63,6 +64,57 @@ struct CellKernel {
         k.smem_bytes = smem();
         return k;
     }
+};
+
+// Launch wrapper of the home-order kernel of the bijection pairing mode
+// (one CTA of NT threads per cell of up to CAPL particles).
+template <class T, int NT, int CAPL>
+struct HomeKernel {
+    static size_t smem() { return home_dyn_smem<T>((uint32_t)CAPL); }
+    static cudaError_t prepare()
+    {
+        static cudaError_t once = cudaFuncSetAttribute(k_home<T, NT, CAPL>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        return once;
+    }
+    static cudaError_t occupancy(int* ctas)
+    {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_home<T, NT, CAPL>, NT, smem());
+    }
+    static cudaError_t occupancy_grid(int* ctas)
+    {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaError_t e = occupancy(&per_sm);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        *ctas = per_sm * sms;
+        return e;
+    }
+    static cudaError_t launch(const CellArgs<T>& a, cudaStream_t st, int grid_ctas)
+    {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        if (grid_ctas <= 0) {
+            e = occupancy_grid(&grid_ctas);
+            if (e != cudaSuccess) return e;
+            if (grid_ctas <= 0) grid_ctas = 1;
+        }
+        k_home<T, NT, CAPL><<<grid_ctas, NT, smem(), st>>>(a);
+        return cudaGetLastError();
+    }
+    static CellKernelEntry entry()
+    {
+        CellKernelEntry k;
+        k.shape = CellShape{1, NT, CAPL / NT};
+        k.launcher = (void*)&launch;
+        k.occupancy = &occupancy_grid_per_sm;
+        k.smem_bytes = smem();
+        return k;
+    }
+    // clusters (here: CTAs) resident on the whole GPU, as CellKernel::occupancy reports
+    static cudaError_t occupancy_grid_per_sm(int* clusters) { return occupancy_grid(clusters); }
 };
 
 }  // namespace ltpc

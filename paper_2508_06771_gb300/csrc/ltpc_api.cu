@@ -123,7 +123,7 @@ int fail_cuda(ltpc_ctx* c, cudaError_t e)
 int set_table(ltpc_ctx* ctx, int table)
 {
     const ClassTable* tabs = nullptr;
-    const int nt = class_tables(ctx->cfg.precision, &tabs);
+    const int nt = class_tables(ctx->cfg.precision, ctx->cfg.pairing_mode, &tabs);
     if (table < 0 || table >= nt) return LTPC_EINVAL;
     const ClassTable& T = tabs[table];
     ctx->table = table;
@@ -189,6 +189,8 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.c_nsig_tot = (T)(ctx->cfg.n_neutral * (ctx->cfg.sigma_el + ctx->cfg.sigma_ion));
     a.c_e_ion = (T)ctx->cfg.e_ion;
     a.c_mratio2 = (T)a.mratio2;
+    a.run_start = ctx->w<uint32_t>(L.run_start);
+    a.run_len = ctx->w<uint32_t>(L.run_len);
     a.order_out = nullptr;
     a.phase_clk = nullptr;
     return a;
@@ -320,11 +322,26 @@ static const ClassTable kTabF64[] = {
     {6, {0, 5, 6, 7, 3, 4}},   // one CTA per cell up to 6144, then clusters of 2/8
     {5, {0, 1, 2, 3, 4}},      // 256-thread CTAs in clusters of 1/2/4/8
 };
-int class_tables(int precision, const ClassTable** out)
+// Bijection pairing mode: the key-sorted sizes (<= 4096) keep their classes;
+// above them the home-order kernel takes what one CTA holds.
+static const ClassTable kTabF32Bij[] = {
+    {6, {0, 5, 10, 8, 9, 4}},  // home order up to 12288, then clusters of 2 and 4 1024-thread CTAs, 8 x 512
+    {5, {0, 5, 10, 3, 4}},     // home order up to 12288, then clusters of 8 (256/512 threads)
+    {6, {0, 5, 6, 8, 9, 4}},   // the cluster kernel (one CTA) up to 12288 instead of the home order
+};
+static const ClassTable kTabF64Bij[] = {
+    {6, {0, 5, 8, 7, 3, 4}},   // home order up to 6144, then clusters of 2/8
+    {6, {0, 5, 6, 7, 3, 4}},   // the cluster kernel up to 6144 instead of the home order
+};
+int class_tables(int precision, int pairing_mode, const ClassTable** out)
 {
-    if (precision == LTPC_F32) { *out = kTabF32; return (int)(sizeof kTabF32 / sizeof kTabF32[0]); }
-    *out = kTabF64;
-    return (int)(sizeof kTabF64 / sizeof kTabF64[0]);
+    const bool bij = pairing_mode == LTPC_PAIR_BIJECTION;
+    if (precision == LTPC_F32) {
+        *out = bij ? kTabF32Bij : kTabF32;
+        return bij ? (int)(sizeof kTabF32Bij / sizeof kTabF32Bij[0]) : (int)(sizeof kTabF32 / sizeof kTabF32[0]);
+    }
+    *out = bij ? kTabF64Bij : kTabF64;
+    return bij ? (int)(sizeof kTabF64Bij / sizeof kTabF64Bij[0]) : (int)(sizeof kTabF64 / sizeof kTabF64[0]);
 }
 }  // namespace ltpc
 
@@ -707,7 +724,7 @@ int ltpc_autotune(ltpc_ctx* ctx, double dt, int32_t* chosen_table)
     (void)dt;
     if (!ctx) return LTPC_EINVAL;
     const ClassTable* tabs = nullptr;
-    const int nt = class_tables(ctx->cfg.precision, &tabs);
+    const int nt = class_tables(ctx->cfg.precision, ctx->cfg.pairing_mode, &tabs);
     // Time a collision-free pass per table: it exercises the same grouping,
     // ordering, staging and reduction work without changing the particles.
     float best = 1e30f;

@@ -114,6 +114,8 @@ struct CellArgs {
     T c_nsig_el, c_nsig_ion;     // n_n sigma_el, n_n sigma_ion
     T c_nsig_tot;                // n_n (sigma_el + sigma_ion), rounded once
     T c_e_ion, c_mratio2;
+    const uint32_t* run_start;   // [M] first index of each cell's loaded run (storage grouped by cell)
+    const uint32_t* run_len;     // [M] its length (0: not grouped)
     uint32_t* order_out;         // optional: pairing order written at I_j + position
     unsigned long long* phase_clk; // optional: SM cycles spent per kernel phase (tracing)
 };

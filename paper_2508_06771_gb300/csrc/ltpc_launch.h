@@ -57,7 +57,9 @@ struct ClassTable {
     int n;
     int kernel[MAX_CLASSES];   // index into the precision's kernel list
 };
-int class_tables(int precision, const ClassTable** out);
+// Tables of a precision and pairing mode (the home-order kernel serves only
+// the bijection mode's tables, and only above its key-sorted sizes).
+int class_tables(int precision, int pairing_mode, const ClassTable** out);
 
 // Host-side launchers of the grouping / bookkeeping kernels (k_group.cu).
 cudaError_t launch_hist(const int32_t* cell, uint32_t* counts, int32_t M, DevState* ds, int grid, cudaStream_t s);
