@@ -98,6 +98,9 @@ def lib():
             L.orc_step.argtypes = [i64p, C.c_int64, C.c_int32, i32p, f64p, f64p, f64p, f64p, f64p, f64p,
                                    f64p, C.POINTER(Params), C.c_uint32, C.c_int, C.c_int, f64p, u32p, i64p]
             L.orc_bij_table.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, u32p, u32p]
+            L.orc_push.argtypes = [C.c_int64, C.c_int32, i32p, f64p, f64p, f64p, f64p, C.c_double, C.c_int, i64p]
+            L.orc_bin.argtypes = [C.c_double, C.c_double, C.c_int32]
+            L.orc_bin.restype = C.c_int
             L.orc_pair_order_mode.argtypes = [C.c_int64, C.c_int32, i32p, u32p, C.POINTER(Params), C.c_uint32,
                                               u64p, u32p]
             _mlp_argtypes(L)
@@ -265,6 +268,23 @@ def neutral(st: State, params: Params, step: int, with_decisions: bool = False):
         out["decision"] = dec[:old]
         out["margin"] = mar[:old]
     return out
+
+
+BOUNDARY_PERIODIC, BOUNDARY_ABSORB = 0, 1
+
+
+def push(st: State, accel: np.ndarray, dx: float, boundary: int = BOUNDARY_PERIODIC) -> int:
+    """Steps S2b/S2c on the oracle state (x along the grid axis, v_z accelerated by the
+    particle's cell field); re-bins the cells; returns how many particles a wall absorbed."""
+    a = np.ascontiguousarray(accel, dtype=np.float64)
+    gone = C.c_int64(0)
+    _check(lib().orc_push(st.n, st.M, _p(st.cell, C.c_int32), _p(st.x, C.c_double), _p(st.vz, C.c_double),
+                          _p(a, C.c_double), _p(st.dt, C.c_double), float(dx), int(boundary), C.byref(gone)))
+    return int(gone.value)
+
+
+def bin_position(x: float, dx: float, M: int) -> int:
+    return lib().orc_bin(float(x), float(dx), int(M))
 
 
 def moments(st: State, params: Params):

@@ -22,6 +22,8 @@
  *   orc_neutral         analytic collision counts, energy bookkeeping
  *   orc_moments         numpy bincount sums
  *   orc_nrl_lnlambda    hand-evaluated formulary values
+ *   orc_push, orc_bin    closed-form free flight, energy gain identity,
+ *                       numpy re-binning and absorbed counts
  *   orc_bij_*, orc_pair_order_mode (bijection mode)
  *                       bijection and inverse on every tested size; chi^2
  *                       uniformity of positions, partners and the left-out
@@ -116,6 +118,7 @@ int orc_group(int64_t n, int32_t M, const int32_t *cell,
     if (n < 0 || M <= 0) return ORC_EINVAL;
     for (int32_t j = 0; j < M; ++j) counts[j] = 0;
     for (int64_t l = 0; l < n; ++l) {
+        if (cell[l] == -1) continue;                            /* removed at a wall (CS7) */
         if (cell[l] < 0 || cell[l] >= M) return ORC_EINVAL;
         counts[cell[l]] += 1;                                   /* CCS1 */
     }
@@ -125,7 +128,8 @@ int orc_group(int64_t n, int32_t M, const int32_t *cell,
     uint64_t *cursor = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)M);
     if (!cursor) return ORC_EINVAL;
     for (int32_t j = 0; j < M; ++j) cursor[j] = cell_start[j];
-    for (int64_t l = 0; l < n; ++l) perm[cursor[cell[l]]++] = (uint32_t)l;   /* CCS3 */
+    for (int64_t l = 0; l < n; ++l)
+        if (cell[l] >= 0) perm[cursor[cell[l]]++] = (uint32_t)l;               /* CCS3 */
     free(cursor);
     return ORC_OK;
 }
@@ -567,6 +571,7 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
         return ORC_EINVAL;
     }
     for (int64_t l = 0; l < n; ++l) {
+        if (cell[l] < 0) continue;                           /* removed at a wall */
         double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
         if (v2 > vmax2[cell[l]]) vmax2[cell[l]] = v2;
     }
@@ -607,12 +612,13 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
     int64_t ncand = 0, nel = 0, nio = 0;
     for (int64_t l = 0; l < n; ++l) {
         int32_t j = cell[l];
+        if (decision) decision[l] = 0;
+        if (j < 0) { if (margin) margin[l] = 1.0; continue; }   /* removed at a wall */
         double numax = p->n_neutral * sig_tot * sqrt(vmax2[j]);
         double pnull = -expm1(-numax * dt[j]);
         uint32_t w[4];
         orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_PARTICLE, w);
         double uc = orc_uniform(w[1]);
-        if (decision) decision[l] = 0;
         int is_cand;
         if (bij && cand[l] != 0) {                 /* cell paired by the bijection */
             is_cand = cand[l] > 0;
@@ -721,6 +727,7 @@ int orc_moments(int64_t n, int32_t M, const int32_t *cell, const double *vx, con
     const double e_over_m = p->charge / p->mass;
     for (int64_t l = 0; l < n; ++l) {
         int32_t j = cell[l];
+        if (j == -1) continue;                               /* removed at a wall */
         if (j < 0 || j >= M) return ORC_EINVAL;
         double *m = mom + 10 * (size_t)j;
         double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
@@ -734,6 +741,63 @@ int orc_moments(int64_t n, int32_t M, const int32_t *cell, const double *vx, con
         m[9] += (E >= p->e_ion ? p->sigma_ion : 0.0) * v;
         if (hist) hist[64 * (size_t)j + (size_t)orc_energy_bin(E)] += 1;
     }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- *
+ * Steps S2b (C2P) and S2c (push) of Table 2, CS6-CS7 of Table 3, on a 1D grid
+ * of M cells of width dx along z (the field axis): Sec. 4.2 uses a constant
+ * grad phi per cell, looked up by the particle's cell, so the acceleration of
+ * particle l is accel[cell_l] (q E / m of its cell, m/s^2).  S2c writes the new
+ * state from the old one:
+ *   x+ = x + dt_j v_z,   v_z+ = v_z + dt_j accel_j,   j = cell_l (before the push);
+ * then the particle is re-binned, cell = floor(x+ / dx) (a1's binning).
+ * Boundary (CS7): periodic -- x+ is brought back into [0, L), L = M dx, by
+ * adding or subtracting L (the displacement per step is below L) -- or
+ * absorbing: a particle with x+ outside [0, L) is removed, which CS7 writes as
+ * w = 0 and this oracle as cell = -1 (its velocity and position are kept and it
+ * takes part in nothing afterwards).  Removed particles (cell < 0) are skipped.
+ * Reading: S2c's Euler update is taken as printed (both from the pre-push
+ * values).  Pinned by the closed-form K-step free flight, the energy gain
+ * m a dx_l + m a^2 dt^2 / 2 per particle and step (an identity of this update),
+ * numpy re-binning counts and absorbed counts (tests/test_oracle_push.py).
+ * ------------------------------------------------------------------------- */
+enum { ORC_BOUNDARY_PERIODIC = 0, ORC_BOUNDARY_ABSORB = 1 };
+
+int orc_bin(double x, double dx, int32_t M)
+{
+    double f = floor(x / dx);
+    if (!(f >= 0.0)) return 0;
+    if (f >= (double)M) return M - 1;
+    return (int32_t)f;
+}
+
+int orc_push(int64_t n, int32_t M, int32_t *cell, double *x, double *vz, const double *accel,
+             const double *dt, double dx, int boundary, int64_t *absorbed)
+{
+    if (n < 0 || M <= 0 || !(dx > 0.0)) return ORC_EINVAL;
+    const double L = dx * (double)M;
+    int64_t gone = 0;
+    for (int64_t l = 0; l < n; ++l) {
+        int32_t j = cell[l];
+        if (j < 0) continue;                               /* removed earlier */
+        if (j >= M) return ORC_EINVAL;
+        double x1 = x[l] + dt[j] * vz[l];
+        double v1 = vz[l] + dt[j] * accel[j];
+        vz[l] = v1;
+        if (boundary == ORC_BOUNDARY_PERIODIC) {
+            if (x1 < 0.0) x1 = x1 + L;
+            else if (x1 >= L) x1 = x1 - L;
+            if (x1 >= L || x1 < 0.0) x1 = 0.0;             /* rounding at the seam */
+            x[l] = x1;
+            cell[l] = orc_bin(x1, dx, M);
+        } else {
+            x[l] = x1;
+            if (x1 < 0.0 || x1 >= L) { cell[l] = -1; ++gone; }
+            else cell[l] = orc_bin(x1, dx, M);
+        }
+    }
+    if (absorbed) *absorbed = gone;
     return ORC_OK;
 }
 

@@ -94,6 +94,26 @@ BIJ_HD uint32_t bij_dec(const BijParams& B, uint32_t y)
     return L * B.b + R;
 }
 
+// The inverse rounds with each round function read from a table: tab[i][R] =
+// bij_round(R, K_i, m_i) for R below the radix of the round's input (b for
+// even i, a for odd i), so the six rounds are six byte loads (the values are
+// below m_i <= 256).  Same result as bij_dec.
+template <class TAB>
+BIJ_HD uint32_t bij_dec_tab(const BijParams& B, const TAB& tab, uint32_t y)
+{
+    uint32_t L = bij_umulhi(y, B.mb);
+    uint32_t R = y - L * B.b;
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        const uint32_t m = (i & 1) ? B.b : B.a;
+        uint32_t t = R + m - (uint32_t)tab(i, L);
+        t = t >= m ? t - m : t;
+        R = L;
+        L = t;
+    }
+    return L * B.b + R;
+}
+
 // pi(r) and its inverse on [0, n) (cycle walking ends: the cycle of r in
 // [0, a b) returns to r < n).
 BIJ_HD uint32_t bij_forward(const BijParams& B, uint32_t r)

@@ -78,7 +78,7 @@ template <class T>
 __host__ __device__ constexpr size_t home_dyn_smem(uint32_t capl)
 {
     return (size_t)3 * (capl + 2u * (16u / sizeof(T))) * sizeof(T) + (((size_t)capl + 7u) & ~(size_t)7u) * 2u +
-           (size_t)capl * 4u;
+           (size_t)(capl / 3u) * 4u;
 }
 
 // Sixteen bytes of one component as W values.
@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
     T* const sv0 = reinterpret_cast<T*>(smem);     // component c at sv0 + c * PAD; home k at slot k + o
     uint16_t* const sinv = reinterpret_cast<uint16_t*>(sv0 + 3 * PAD);   // home index at each pairing position
     uint32_t* const sid = reinterpret_cast<uint32_t*>(sinv + ((CAPL + 7) & ~7));   // ids of the appended homes
+    constexpr uint32_t SIDCAP = CAPL / 3;          // appended homes whose ids the table holds
     __shared__ __align__(8) uint64_t s_bar;        // completion of the bulk loads
     __shared__ uint4 s_item[2];                    // current / next work item {j, N_j, I_j, valid}
     __shared__ __align__(16) uint32_t s_bij[2][12];// bijection words (CPB_*) of the current / next cell
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
     __shared__ uint32_t s_ioff[CAPL / 32];         // ionizations before each mask word
     __shared__ T s_par[16];
     __shared__ typename MaxBits<T>::U s_vmax;
+    __shared__ __align__(16) uint8_t s_rt[2][6][256];  // round functions of the current / next cell's bijection
 
     const unsigned tid = threadIdx.x;
     DevState* ds = a.ds;
@@ -162,13 +164,28 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
         mbar_init(&s_bar, 1u);
         fence_mbar_init();
     }
+    // a cell's six round functions as byte tables (round i reads R below b for even i, a for
+    // odd i), by every thread but the last warp's
+    auto fill_round_tables = [&](uint32_t b) {
+        const uint32_t ab = s_bij[b][CPB_AB];
+        if (ab == 0u || tid >= NT - 32u) return;
+        const uint32_t A_ = ab & 0xFFFFu, B_ = ab >> 16;
+        for (uint32_t e = tid; e < 6u * 256u; e += NT - 32u) {
+            const uint32_t i = e >> 8, r = e & 255u;
+            const uint32_t m = (i & 1u) ? B_ : A_, lim = (i & 1u) ? A_ : B_;
+            if (r < lim) s_rt[b][i][r] = (uint8_t)bij_round(r, s_bij[b][CPB_KEY + i], m);
+        }
+    };
     if (tid == TK) {
         const uint32_t w = atomicAdd(&ds->ticket[a.cls], 1u);
         const uint4 it = w < list_n ? a.list[w] : make_uint4(0u, 0u, 0u, 0u);
         s_item[0] = it;
         if (it.w != 0u) fetch_cell_words(it.x, 0u);
+        else s_bij[0][CPB_AB] = 0u;
         cp_async_wait_all();
     }
+    __syncthreads();
+    fill_round_tables(0u);
     __syncthreads();
     PhaseClock pc{a.phase_clk, 0};
     pc.start();
@@ -187,8 +204,11 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                 const uint4 it = wn < list_n ? a.list[wn] : make_uint4(0u, 0u, 0u, 0u);
                 s_item[par ^ 1u] = it;
                 if (it.w != 0u) fetch_cell_words(it.x, par ^ 1u);
+                else s_bij[par ^ 1u][CPB_AB] = 0u;
                 cp_async_wait_all();
             }
+            __syncthreads();
+            fill_round_tables(par ^ 1u);
             __syncthreads();
             continue;
         }
@@ -205,7 +225,9 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
         // the plain-access homes in order: [0, nhead), [ktail, rl), [rl, n)
         auto plain_home = [&](uint32_t t) -> uint32_t { return t < nhead ? t : t - nhead + ktail; };
         // id of home k: in the run, or (appended) from the table filled in step 1
-        auto id_of = [&](uint32_t k) -> uint32_t { return k < rl ? rs + k : sid[k - rl]; };
+        auto id_of = [&](uint32_t k) -> uint32_t {
+            return k < rl ? rs + k : (k - rl < SIDCAP ? sid[k - rl] : __ldg(a.perm + s + k));
+        };
 
         // ---- 1. loads.  Thread 0 waits until the previous cell's bulk stores have read the
         // slots (that drain overlaps the bijection work below), then issues the run interior
@@ -230,32 +252,32 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
         if (tid < nplain) {
             pk0 = plain_home(tid);
             pl0 = pk0 < rl ? rs + pk0 : __ldg(a.perm + s + pk0);
-            if (pk0 >= rl) sid[pk0 - rl] = pl0;
+            if (pk0 >= rl && pk0 - rl < SIDCAP) sid[pk0 - rl] = pl0;
             pvx = gv[0][pl0]; pvy = gv[1][pl0]; pvz = gv[2][pl0];
         }
         for (uint32_t t = tid + NT; t < nplain; t += NT) {   // more than NT plain homes: ids only here
             const uint32_t k = plain_home(t);
-            if (k >= rl) sid[k - rl] = __ldg(a.perm + s + k);
+            if (k >= rl && k - rl < SIDCAP) sid[k - rl] = __ldg(a.perm + s + k);
         }
         uint32_t wn = 0u;
         if (tid == TK) wn = atomicAdd(&ds->ticket[a.cls], 1u);
         for (uint32_t i = tid; i < 4u * NBIN; i += NT) s_hist[i] = 0u;
         for (uint32_t i = tid; i < (n + 31u) / 32u; i += NT) s_imask[i] = 0u;
+        BijParams B;
+        B.n = n; B.a = bij_ab & 0xFFFFu; B.b = bij_ab >> 16; B.mb = bw[CPB_MB];
         pc.mark(0);
 
         // ---- 2. the pairing bijection, inverted for this thread's pair slots while the copies
         // fly: one pass of the rounds for every position (independent chains), then the rare
         // images at or above n walk on; the home of each position also goes to the table
-        BijParams B;
-        B.n = n; B.a = bij_ab & 0xFFFFu; B.b = bij_ab >> 16; B.mb = bw[CPB_MB];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) B.key[q] = bw[CPB_KEY + q];
+        const uint8_t(*const rtab)[256] = s_rt[par];       // filled during the previous cell
+        auto rt = [&](int i, uint32_t r) -> uint32_t { return rtab[i][r]; };
         uint32_t hx[2 * PS];
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
             const uint32_t p = tid + (uint32_t)i * NT;
-            hx[2 * i] = 2u * p < n ? bij_dec(B, 2u * p) : 0u;
-            hx[2 * i + 1] = 2u * p + 1u < n ? bij_dec(B, 2u * p + 1u) : 0u;
+            hx[2 * i] = 2u * p < n ? bij_dec_tab(B, rt, 2u * p) : 0u;
+            hx[2 * i + 1] = 2u * p + 1u < n ? bij_dec_tab(B, rt, 2u * p + 1u) : 0u;
         }
         uint32_t pk[PS];                                   // home indices of positions 2p | 2p+1 << 16
 #pragma unroll
@@ -264,10 +286,10 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             pk[i] = 0u;
             if (2u * p < n) {
                 uint32_t ka = hx[2 * i], kb = hx[2 * i + 1];
-                while (ka >= n) ka = bij_dec(B, ka);
+                while (ka >= n) ka = bij_dec_tab(B, rt, ka);
                 const bool two = 2u * p + 1u < n;
                 if (two) {
-                    while (kb >= n) kb = bij_dec(B, kb);
+                    while (kb >= n) kb = bij_dec_tab(B, rt, kb);
                 }
                 pk[i] = ka | (kb << 16);
                 sinv[2u * p] = (uint16_t)ka;
@@ -286,7 +308,10 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
 
         // ---- 3. wait for the copies (bounded), then every thread sees every slot
         if (tid == DM || tid == TK) cp_async_wait_all();
-        if (tid == TK && s_item[par ^ 1u].w != 0u) fetch_cell_words(s_item[par ^ 1u].x, par ^ 1u);   // waited at the end
+        if (tid == TK) {                                   // waited before the barrier after S1
+            if (s_item[par ^ 1u].w != 0u) fetch_cell_words(s_item[par ^ 1u].x, par ^ 1u);
+            else s_bij[par ^ 1u][CPB_AB] = 0u;
+        }
         bool done = false;
         for (uint32_t it = 0; it < MBAR_SPIN_LIMIT && !done; ++it) done = mbar_try_wait(&s_bar, phase);
         if (__syncthreads_or(done ? 0 : 1)) {
@@ -388,8 +413,10 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                 }
             }
         }
+        if (tid == TK) cp_async_wait_all();                // the next cell's words, for the tables below
         __syncthreads();
         pc.mark(7);
+        fill_round_tables(par ^ 1u);                       // the next cell's round functions
 
         // ---- 5. one sweep of the home slots (16-byte vectors): the restoration, the largest
         // squared speed, and the moments of the result (S3a/S3b, Sec. 4.5) with the energy
@@ -586,7 +613,6 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             for (int c = 0; c < 3; ++c) gv[c][l] = sv0[c * PAD + k + o];
         }
         if (tid == TK) {
-            cp_async_wait_all();                           // the next cell's words
             const uint4 nx = s_item[par ^ 1u];             // this thread's own copy, waited in step 3
             if (nx.w != 0u && nx.y != 0u) {
                 const uint32_t nrs = s_run[par ^ 1u][0], nrl = min(s_run[par ^ 1u][1], nx.y);
