@@ -125,7 +125,8 @@ void ltpc_destroy(ltpc_ctx* ctx);
 #define LTPC_LOAD_SRC_DEVICE 1   /* sources are device pointers (else host memory) */
 #define LTPC_LOAD_ASYNC 2        /* do not wait on the stream; report device-detected errors later */
 
-/* Load n particles: cell ids (int32, in [0, M)), optional positions x (only
+/* Load n particles: cell ids (int32, in [0, M); NULL to bin the positions
+ * when a field is set, see ltpc_set_field), optional positions x (only
  * if has_position, else ignored), velocities vx, vy, vz in the context's
  * precision.  flags: LTPC_LOAD_SRC_DEVICE selects device sources (host
  * sources should be pinned for full copy bandwidth); LTPC_LOAD_ASYNC makes
@@ -141,6 +142,34 @@ void ltpc_destroy(ltpc_ctx* ctx);
  * sources must stay unchanged until the stream reaches the copy). */
 int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const void* x,
                         const void* vx, const void* vy, const void* vz, int flags);
+
+/* Walls of ltpc_set_field. */
+#define LTPC_WALL_PERIODIC 0     /* a particle leaving [0, L) re-enters at the other end    */
+#define LTPC_WALL_ABSORB 1       /* CS7: it is removed (cell id -1, slot kept, no effect)    */
+
+/* Steps S2b/S2c of Table 2 (CS6/CS7 of Table 3): a constant field per cell and
+ * the particle push.  Geometry: the n_cells cells are a 1D grid of width dx [m]
+ * along z, the domain [0, L), L = n_cells dx, and x is the position along it.
+ * accel (host [n_cells], m/s^2) is q E_j / m of each cell (Sec. 4.2 uses a
+ * constant grad phi per cell, looked up by the particle's cell).  The push,
+ * as S2c writes it, from the pre-push state of particle l in cell j:
+ *   x+ = x + dt_j v_z,   v_z+ = v_z + dt_j accel_j,   then cell = floor(x+ / dx),
+ * and `boundary` (LTPC_WALL_*) handles the walls.  Once a field is set,
+ * ltpc_step and ltpc_run end every step with the push of every particle
+ * (secondaries of the step included, from their parent's position), the
+ * per-cell grouping of the new cells (CCS1-CCS3 every step) and the moments
+ * of the pushed particles (S3 follows S2c), which ltpc_moments then returns;
+ * ltpc_collide_coulomb and ltpc_collide_neutral do not push.  A load may then
+ * pass cell = NULL with positions: each cell id is floor(x / dx) (positions
+ * outside [0, L) are rejected with EINVAL).  Needs has_position and
+ * LTPC_PAIR_KEY (a push breaks the grouping of storage by cell that the
+ * bijection mode relies on).  Synchronizing.  Errors: EINVAL. */
+int ltpc_set_field(ltpc_ctx* ctx, double dx, const double* accel, int32_t boundary);
+
+/* Steps S2b/S2c alone (no collisions) with time step dt (cell j: dt *
+ * dt_factor[j]) at step number `step`, then the grouping of the new cells and
+ * their moments.  Needs ltpc_set_field.  Asynchronous.  Errors: EINVAL. */
+int ltpc_push(ltpc_ctx* ctx, double dt, int64_t step);
 
 /* Step S1 only: Takizuka-Abe Coulomb collisions (Sec. 4.4) with time step
  * dt (cell j uses dt * dt_factor[j]) at step number `step` (0 <= step <

@@ -684,7 +684,7 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
             rc = ORC_EINVAL;
         } else {
             int64_t dst = n;
-            for (int64_t k = 0; k < n; ++k) {
+            for (int64_t k = 0; k < (int64_t)cs[M]; ++k) {   /* live particles (removed ones are not listed) */
                 uint32_t l = order[k];
                 if (!ionize[l]) continue;
                 vx[dst] = sec[3 * l + 0]; vy[dst] = sec[3 * l + 1]; vz[dst] = sec[3 * l + 2];

@@ -31,7 +31,7 @@ struct Layout {
     size_t vx, vy, vz, cell, x;
     // work offsets
     size_t perm, counts, cell_start, cs_prev, cursor, ion_count, ion_off, stage_l, stage_vx, stage_vy,
-        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, lists, ds;
+        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, accel, lists, ds;
 };
 
 bool compute_layout(const ltpc_config* c, Layout* L)
@@ -69,6 +69,7 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->run_start = take(M * 4);
     L->run_len = take(M * 4);
     L->aslot = take(cap * 4);
+    L->accel = take(M * 8);
     L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
     L->work = o;
@@ -100,6 +101,10 @@ struct ltpc_ctx {
     uint32_t graph_flags = 0;
     int64_t next_step = -1;
     double cur_dt = std::nan("");
+    // field and push (ltpc_set_field)
+    bool field = false;
+    double dx = 0.0;
+    int32_t wall = LTPC_WALL_PERIODIC;
     char cuda_err[256] = {0};
 
     template <class P> P* w(size_t off) const { return reinterpret_cast<P*>(wk + off); }
@@ -199,8 +204,35 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
 // Enqueue one pass: scatter (CCS3), the cell kernel per class, then the
 // bookkeeping that appends secondaries and regroups for the next pass.
 template <class T>
+int enqueue_body(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out, cudaStream_t s,
+                 cudaEvent_t* ev, unsigned long long* phase_clk);
+
+// With F_PUSH: the collisions (S1, S2a) and their appends, then steps S2b/S2c
+// on every particle, CCS1-CCS2 of the new cells, and a pass of moments (S3 of
+// the pushed particles in their new cells, which the next pass also starts from).
+template <class T>
 int enqueue_pass(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out, cudaStream_t s,
                  cudaEvent_t* ev = nullptr, unsigned long long* phase_clk = nullptr)
+{
+    if (!(flags & F_PUSH) || !ctx->field) return enqueue_body<T>(ctx, flags & ~F_PUSH, advance, order_out, s, ev, phase_clk);
+    const Layout& L = ctx->L;
+    int rc = enqueue_body<T>(ctx, flags & ~F_PUSH, false, order_out, s, nullptr, phase_clk);
+    if (rc) return rc;
+    CK(launch_push<T>(ctx->s<T>(L.x), ctx->s<T>(L.vz), ctx->s<int32_t>(L.cell), ctx->w<double>(L.accel),
+                      ctx->w<double>(L.cpar), ctx->cfg.n_cells, ctx->dx, ctx->wall == LTPC_WALL_ABSORB ? 1 : 0,
+                      ctx->w<uint32_t>(L.run_len), ctx->ds, ctx->sms * 8, s));
+    CK(cudaMemsetAsync(ctx->w<uint32_t>(L.counts), 0, (size_t)ctx->cfg.n_cells * 4, s));
+    CK(launch_hist_step(ctx->s<int32_t>(L.cell), ctx->w<uint32_t>(L.counts), ctx->cfg.n_cells, ctx->ds, ctx->sms * 8, s));
+    CK(launch_regroup(ctx->cfg.n_cells, ctx->w<uint32_t>(L.counts), ctx->w<uint32_t>(L.cell_start),
+                      ctx->w<uint32_t>(L.cs_prev), ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.ion_count),
+                      ctx->w<uint32_t>(L.ion_off), ctx->lists, (unsigned long long)ctx->cfg.capacity, 0, 0, ctx->ds,
+                      s));
+    return enqueue_body<T>(ctx, 0u, advance, nullptr, s, nullptr, nullptr);
+}
+
+template <class T>
+int enqueue_body(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_out, cudaStream_t s,
+                 cudaEvent_t* ev, unsigned long long* phase_clk)
 {
     const Layout& L = ctx->L;
     const int grid_stream = ctx->sms * 8;
@@ -272,6 +304,7 @@ uint32_t step_flags(const ltpc_ctx* ctx, bool coulomb, bool neutral)
         if (ctx->cfg.lnlambda_mode == LTPC_LNL_NRL) f |= F_LNL_NRL;
     }
     if (neutral && ctx->cfg.n_neutral > 0.0) f |= F_NEUTRAL;
+    if (ctx->field) f |= F_PUSH;
     return f;
 }
 
@@ -439,7 +472,8 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
                         const void* vy, const void* vz, int flags)
 {
     if (!ctx || n < 0 || n > ctx->cfg.capacity) return LTPC_EINVAL;
-    if (n > 0 && (!cell || !vx || !vy || !vz)) return LTPC_EINVAL;
+    const bool bin = !cell && ctx->field && ctx->cfg.has_position && x;   // cell = floor(x / dx)
+    if (n > 0 && ((!cell && !bin) || !vx || !vy || !vz)) return LTPC_EINVAL;
     if (flags & ~(LTPC_LOAD_SRC_DEVICE | LTPC_LOAD_ASYNC)) return LTPC_EINVAL;
     const bool async = (flags & LTPC_LOAD_ASYNC) != 0;
     const Layout& L = ctx->L;
@@ -450,10 +484,18 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
         CK(cudaMemcpyAsync(ctx->st + L.vx, vx, nb, kind, s));
         CK(cudaMemcpyAsync(ctx->st + L.vy, vy, nb, kind, s));
         CK(cudaMemcpyAsync(ctx->st + L.vz, vz, nb, kind, s));
-        CK(cudaMemcpyAsync(ctx->st + L.cell, cell, (size_t)n * 4, kind, s));
+        if (cell) CK(cudaMemcpyAsync(ctx->st + L.cell, cell, (size_t)n * 4, kind, s));
         if (ctx->cfg.has_position && x) CK(cudaMemcpyAsync(ctx->st + L.x, x, nb, kind, s));
     }
     CK(launch_set_state(ctx->ds, (unsigned long long)n, 1, 0u, 0.0, 0, s));
+    if (bin && n > 0) {
+        if (ctx->cfg.precision == LTPC_F32)
+            CK(launch_bin<float>(ctx->s<float>(L.x), ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->dx, ctx->ds,
+                                 ctx->sms * 4, s));
+        else
+            CK(launch_bin<double>(ctx->s<double>(L.x), ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->dx, ctx->ds,
+                                  ctx->sms * 4, s));
+    }
     CK(cudaMemsetAsync(ctx->w<uint32_t>(L.counts), 0, (size_t)ctx->cfg.n_cells * 4, s));
     CK(cudaMemsetAsync(ctx->w<uint32_t>(L.ion_count), 0, (size_t)ctx->cfg.n_cells * 4, s));
     CK(cudaMemsetAsync(&ctx->ds->err, 0, 4, s));
@@ -479,16 +521,39 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
     return async ? LTPC_OK : read_errors(ctx);
 }
 
+int ltpc_set_field(ltpc_ctx* ctx, double dx, const double* accel, int32_t boundary)
+{
+    if (!ctx || !(dx > 0.0) || !std::isfinite(dx) || !accel) return LTPC_EINVAL;
+    if (boundary != LTPC_WALL_PERIODIC && boundary != LTPC_WALL_ABSORB) return LTPC_EINVAL;
+    if (!ctx->cfg.has_position || ctx->cfg.pairing_mode != LTPC_PAIR_KEY) return LTPC_EINVAL;
+    const size_t M = (size_t)ctx->cfg.n_cells;
+    for (size_t j = 0; j < M; ++j)
+        if (!std::isfinite(accel[j])) return LTPC_EINVAL;
+    CK(cudaMemcpyAsync(ctx->w<double>(ctx->L.accel), accel, M * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->field = true;
+    ctx->dx = dx;
+    ctx->wall = boundary;
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    return LTPC_OK;
+}
+
+int ltpc_push(ltpc_ctx* ctx, double dt, int64_t step)
+{
+    if (!ctx || !ctx->field) return LTPC_EINVAL;
+    return run_pass(ctx, dt, step, F_PUSH);
+}
+
 int ltpc_collide_coulomb(ltpc_ctx* ctx, double dt, int64_t step)
 {
     if (!ctx) return LTPC_EINVAL;
-    return run_pass(ctx, dt, step, step_flags(ctx, true, false));
+    return run_pass(ctx, dt, step, step_flags(ctx, true, false) & ~F_PUSH);
 }
 
 int ltpc_collide_neutral(ltpc_ctx* ctx, double dt, int64_t step)
 {
     if (!ctx) return LTPC_EINVAL;
-    return run_pass(ctx, dt, step, step_flags(ctx, false, true));
+    return run_pass(ctx, dt, step, step_flags(ctx, false, true) & ~F_PUSH);
 }
 
 int ltpc_step(ltpc_ctx* ctx, double dt, int64_t step)
@@ -534,7 +599,7 @@ int ltpc_profile_step(ltpc_ctx* ctx, double dt, int64_t step, float* ms, int32_t
         if (e != cudaSuccess) { rc = fail_cuda(ctx, e); break; }
     }
     if (rc == LTPC_OK) rc = set_state(ctx, step, dt);
-    if (rc == LTPC_OK) rc = enqueue(ctx, step_flags(ctx, true, true), true, nullptr, ctx->stream, ev);
+    if (rc == LTPC_OK) rc = enqueue(ctx, step_flags(ctx, true, true) & ~F_PUSH, true, nullptr, ctx->stream, ev);
     if (rc == LTPC_OK) {
         cudaError_t e = cudaEventSynchronize(ev[nk]);
         for (int k = 0; k < nk && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
@@ -552,7 +617,7 @@ int ltpc_profile_phases(ltpc_ctx* ctx, double dt, int64_t step, unsigned long lo
     if (!ctx || !d_cycles) return LTPC_EINVAL;
     CK(cudaMemsetAsync(d_cycles, 0, 16 * sizeof(unsigned long long), ctx->stream));
     int rc = set_state(ctx, step, dt);
-    if (rc == LTPC_OK) rc = enqueue(ctx, step_flags(ctx, true, true), true, nullptr, ctx->stream, nullptr, d_cycles);
+    if (rc == LTPC_OK) rc = enqueue(ctx, step_flags(ctx, true, true) & ~F_PUSH, true, nullptr, ctx->stream, nullptr, d_cycles);
     ctx->next_step = step + 1;
     ctx->cur_dt = dt;
     return rc;

@@ -24,6 +24,7 @@ enum : uint32_t {
     F_NEUTRAL = 2u,          // step S2a: electron-neutral null-collision sampling
     F_CORRECTION = 4u,       // restore per-cell momentum and energy after S1
     F_LNL_NRL = 8u,          // Coulomb logarithm from the cell's previous moments
+    F_PUSH = 16u,            // host only: the pass ends with steps S2b/S2c (a field is set)
 };
 
 constexpr int MAX_CLASSES = 8;

@@ -79,6 +79,13 @@ cudaError_t launch_append(int32_t M, const uint32_t* ion_off, const uint32_t* cs
                           uint32_t* aslot, const DevState* ds, int grid, cudaStream_t s);
 cudaError_t launch_set_state(DevState* ds, unsigned long long n, int set_n, uint32_t step, double dt, int set_step,
                              cudaStream_t s);
+// Steps S2b/S2c and the per-step grouping after them (k_push.cu).
+template <class T>
+cudaError_t launch_push(T* x, T* vz, int32_t* cell, const double* accel, const double* cpar, int32_t M, double dx,
+                        int absorb, uint32_t* run_len, DevState* ds, int grid, cudaStream_t s);
+cudaError_t launch_hist_step(const int32_t* cell, uint32_t* counts, int32_t M, DevState* ds, int grid, cudaStream_t s);
+template <class T>
+cudaError_t launch_bin(const T* x, int32_t* cell, int32_t M, double dx, DevState* ds, int grid, cudaStream_t s);
 template <class T>
 cudaError_t launch_check_finite(const T* vx, const T* vy, const T* vz, DevState* ds, int grid, cudaStream_t s);
 

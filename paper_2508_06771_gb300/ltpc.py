@@ -21,6 +21,7 @@ F32, F64 = 0, 1
 LOAD_SRC_DEVICE, LOAD_ASYNC = 1, 2   # flags of ltpc_load_particles
 LNL_CONST, LNL_NRL = 0, 1
 PAIR_KEY, PAIR_BIJECTION = 0, 1      # ltpc_config.pairing_mode
+WALL_PERIODIC, WALL_ABSORB = 0, 1    # ltpc_set_field
 
 _lock = threading.Lock()
 _lib = None
@@ -65,6 +66,8 @@ def load_library(path: str = LIB_PATH):
             "ltpc_create": (C.c_int, [C.POINTER(vp), cfgp, vp, vp, vp]),
             "ltpc_destroy": (None, [vp]),
             "ltpc_load_particles": (C.c_int, [vp, i64, vp, vp, vp, vp, vp, C.c_int]),
+            "ltpc_set_field": (C.c_int, [vp, C.c_double, vp, i32]),
+            "ltpc_push": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_collide_coulomb": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_collide_neutral": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_step": (C.c_int, [vp, C.c_double, i64]),
@@ -211,12 +214,21 @@ class Collider:
         return t.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=self.device)
 
     # ------------------------------------------------------------------ API
+    def set_field(self, dx: float, accel, boundary: int = WALL_PERIODIC):
+        """Steps S2b/S2c: cells of width dx along z, per-cell acceleration accel [M] (m/s^2)."""
+        self._accel = np.ascontiguousarray(accel, dtype=np.float64)
+        self._check(self.L.ltpc_set_field(self.ctx, float(dx), self._accel.ctypes.data, int(boundary)), "set_field")
+
+    def push(self, dt, step):
+        self._check(self.L.ltpc_push(self.ctx, float(dt), int(step)), "push")
+
     def load(self, vx, vy, vz, cell, x=None):
-        """Load particles from numpy arrays or tensors (copied to the device first)."""
+        """Load particles from numpy arrays or tensors (copied to the device first); cell=None
+        bins the positions (needs a field, see set_field)."""
         t = self.torch
-        n = int(len(cell))
+        n = int(len(vx))
         vxd, vyd, vzd = (self._dev(v, self.dtype) for v in (vx, vy, vz))
-        cd = self._dev(cell, t.int32)
+        cd = self._dev(cell, t.int32) if cell is not None else None
         xd = self._dev(x, self.dtype) if x is not None else None
         self._check(self.L.ltpc_load_particles(self.ctx, n, _ptr(cd), _ptr(xd), _ptr(vxd), _ptr(vyd), _ptr(vzd),
                                                LOAD_SRC_DEVICE),

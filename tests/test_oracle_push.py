@@ -102,3 +102,9 @@ def test_absorbing_walls(orc):
     assert np.abs(e1 - e0).max() <= 1e-12 * e0.max()
     assert orc.push(st, np.zeros(M), dx, orc.BOUNDARY_ABSORB) >= 0
     assert np.all(st.cell[:st.n][out] == -1)
+    # the neutral step (with ionization appends) leaves the removed particles alone too
+    n_before, dead = st.n, st.cell[:st.n] < 0
+    info = orc.neutral(st, P, 2, with_decisions=True)
+    assert info["candidates"] > 0 and np.all(info["decision"][dead] == 0)
+    assert st.n == n_before + info["ionization"]
+    assert np.all(st.cell[n_before:st.n] >= 0)
