@@ -99,6 +99,8 @@ def lib():
                                    f64p, C.POINTER(Params), C.c_uint32, C.c_int, C.c_int, f64p, u32p, i64p]
             L.orc_bij_table.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, u32p, u32p]
             L.orc_push.argtypes = [C.c_int64, C.c_int32, i32p, f64p, f64p, f64p, f64p, C.c_double, C.c_int, i64p]
+            L.orc_recombine.argtypes = [C.c_int64, C.c_int32, i32p, u32p, f64p, f64p, f64p, f64p, f64p,
+                                        C.POINTER(Params), C.c_uint32, C.c_double, C.c_double, i64p]
             L.orc_bin.argtypes = [C.c_double, C.c_double, C.c_int32]
             L.orc_bin.restype = C.c_int
             L.orc_pair_order_mode.argtypes = [C.c_int64, C.c_int32, i32p, u32p, C.POINTER(Params), C.c_uint32,
@@ -280,6 +282,18 @@ def push(st: State, accel: np.ndarray, dx: float, boundary: int = BOUNDARY_PERIO
     gone = C.c_int64(0)
     _check(lib().orc_push(st.n, st.M, _p(st.cell, C.c_int32), _p(st.x, C.c_double), _p(st.vz, C.c_double),
                           _p(a, C.c_double), _p(st.dt, C.c_double), float(dx), int(boundary), C.byref(gone)))
+    return int(gone.value)
+
+
+def recombine(st: State, params: Params, step: int, k_rec: float, de_rec: float) -> int:
+    """Recombination C5 (RS0-RS5) on the oracle state after the neutral step of `step`;
+    returns how many primaries were removed."""
+    gone = C.c_int64(0)
+    ids = getattr(st, "ids", None)
+    _check(lib().orc_recombine(st.n, st.M, _p(st.cell, C.c_int32), _p(ids, C.c_uint32), _p(st.vx, C.c_double),
+                               _p(st.vy, C.c_double), _p(st.vz, C.c_double), _p(st.inv_vol, C.c_double),
+                               _p(st.dt, C.c_double), C.byref(params), step, float(k_rec), float(de_rec),
+                               C.byref(gone)))
     return int(gone.value)
 
 

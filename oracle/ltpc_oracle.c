@@ -22,6 +22,8 @@
  *   orc_neutral         analytic collision counts, energy bookkeeping
  *   orc_moments         numpy bincount sums
  *   orc_nrl_lnlambda    hand-evaluated formulary values
+ *   orc_recombine       count law, unique matching, removed count, energy
+ *                       bookkeeping
  *   orc_push, orc_bin    closed-form free flight, energy gain identity,
  *                       numpy re-binning and absorbed counts
  *   orc_bij_*, orc_pair_order_mode (bijection mode)
@@ -38,7 +40,8 @@
 #define ORC_PI 3.14159265358979323846
 
 /* Random-stream tags: which use a Philox block serves (counter word 2). */
-enum { ORC_TAG_PARTICLE = 1, ORC_TAG_PAIR = 2, ORC_TAG_SCATTER = 3, ORC_TAG_SECONDARY = 4, ORC_TAG_PERM = 5 };
+enum { ORC_TAG_PARTICLE = 1, ORC_TAG_PAIR = 2, ORC_TAG_SCATTER = 3, ORC_TAG_SECONDARY = 4, ORC_TAG_PERM = 5,
+       ORC_TAG_RECOMB = 6 };
 
 /* Pairing modes (see orc_pair_order_ids).  In the bijection mode, cells of at
  * least ORC_BIJ_MIN_N particles are paired through a keyed bijection of their
@@ -741,6 +744,73 @@ int orc_moments(int64_t n, int32_t M, const int32_t *cell, const double *vx, con
         m[9] += (E >= p->e_ion ? p->sigma_ion : 0.0) * v;
         if (hist) hist[64 * (size_t)j + (size_t)orc_energy_bin(E)] += 1;
     }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- *
+ * Recombination C5 (Table 1: Ar+ + 2e -> Ar_m + e), the kernel of Sec. 4.3 and
+ * Table 4 (RS0-RS5), run after C1/C2 in step S2a.  Every cell j with N_j
+ * particles at the start of the step (the ones of this step's pairing order):
+ *   RS0  the primaries: the paper takes them from CS3's per-particle
+ *        probabilities.  Reading: a three-body rate k_rec [m^6/s] with the ion
+ *        density equal to the electron density n_j = w N_j / V_j gives every
+ *        electron P_rec = 1 - exp(-dt_j k_rec n_j^2); as for the null-collision
+ *        candidates, the cell takes n_p = floor(P_rec N_j + U) of them (U from
+ *        the Philox block (cell, step, RECOMB, 0), word 0), capped at N_j / 2,
+ *        at the last n_p positions of the pairing order (a uniformly random
+ *        subset);
+ *   RS1  the catalyte list C_j: the cell's other particles; the paper builds it
+ *        with an atomic cursor, here it is the pairing order itself;
+ *   RS2-RS3  each primary pops a distinct catalyte: the r-th primary (position
+ *        N_j - n_p + r) takes the catalyte at position N_j - 2 n_p + r;
+ *   RS4  the catalyte takes the primary's kinetic energy, its own and the
+ *        released energy dE_rec [eV] (reading: the binding energy left over
+ *        when Ar_m forms), in an isotropic direction from words 0-1 of its
+ *        RECOMB block;
+ *   RS5  the primary is removed (w = 0; here cell = -1, as at an absorbing wall).
+ * Pinned by the count law (floor/ceil of P_rec N, mean P_rec N), the unique
+ * matching within cells, the removed count and the energy bookkeeping
+ * (tests/test_oracle_recombination.py).
+ * ------------------------------------------------------------------------- */
+int orc_recombine(int64_t n, int32_t M, int32_t *cell, const uint32_t *ids, double *vx, double *vy, double *vz,
+                  const double *inv_vol, const double *dt, const orc_params *p, uint32_t step, double k_rec,
+                  double de_rec, int64_t *removed)
+{
+    if (n < 0 || M <= 0) return ORC_EINVAL;
+    uint64_t *cs = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)M + 1));
+    uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    if (!cs || !order) { free(cs); free(order); return ORC_EINVAL; }
+    int rc = orc_pair_order_mode(n, M, cell, ids, p, step, cs, order);
+    if (rc) { free(cs); free(order); return rc; }
+    const double e_over_m = p->charge / p->mass;
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    int64_t gone = 0;
+    for (int32_t j = 0; j < M; ++j) {
+        uint64_t s = cs[j], cnt = cs[j + 1] - cs[j];
+        if (cnt < 2) continue;
+        double nj = p->weight * (double)cnt * inv_vol[j];
+        double prec = -expm1(-dt[j] * k_rec * nj * nj);
+        uint32_t ctr[4] = {(uint32_t)orc_cell_id(p, j), step, ORC_TAG_RECOMB, 0u}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        double t = prec * (double)cnt + orc_uniform(w[0]);
+        uint64_t np_ = (uint64_t)floor(t);
+        if (np_ > cnt / 2) np_ = cnt / 2;
+        for (uint64_t r = 0; r < np_; ++r) {
+            uint32_t lp = order[s + cnt - np_ + r], lc = order[s + cnt - 2 * np_ + r];
+            double ep = 0.5 * (vx[lp] * vx[lp] + vy[lp] * vy[lp] + vz[lp] * vz[lp]) / e_over_m;
+            double ec = 0.5 * (vx[lc] * vx[lc] + vy[lc] * vy[lc] + vz[lc] * vz[lc]) / e_over_m;
+            double sp = sqrt(2.0 * (ec + ep + de_rec) * e_over_m);
+            uint32_t c[4];
+            orc_draw(p->seed, orc_id(ids, lc), step, ORC_TAG_RECOMB, c);
+            double d[3];
+            orc_iso_dir(c[0], c[1], d);
+            vx[lc] = sp * d[0]; vy[lc] = sp * d[1]; vz[lc] = sp * d[2];
+            cell[lp] = -1;
+            ++gone;
+        }
+    }
+    free(cs); free(order);
+    if (removed) *removed = gone;
     return ORC_OK;
 }
 
