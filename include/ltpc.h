@@ -171,6 +171,22 @@ int ltpc_set_field(ltpc_ctx* ctx, double dx, const double* accel, int32_t bounda
  * their moments.  Needs ltpc_set_field.  Asynchronous.  Errors: EINVAL. */
 int ltpc_push(ltpc_ctx* ctx, double dt, int64_t step);
 
+/* Recombination C5 of Table 1 (Ar+ + 2e -> Ar_m + e; Sec. 4.3, Table 4
+ * RS0-RS5), run in step S2a after C1/C2 by ltpc_step and ltpc_collide_neutral.
+ * k_rec [m^6/s]: three-body rate with the ion density taken equal to the
+ * electron density, so every electron of cell j recombines with probability
+ * P_rec = 1 - exp(-dt_j k_rec n_j^2); de_rec [eV]: energy the catalyte gains
+ * besides the primary's kinetic energy.  Each cell takes floor(P_rec N_j + U)
+ * primaries (U from the cell's RECOMB Philox block; at most N_j / 2) at the
+ * last positions of the step's pairing order; the r-th primary hands its
+ * energy to the catalyte n_p positions before it (a unique match inside the
+ * cell, in place of the paper's atomic catalyte list) and is removed: its
+ * cell id becomes -1 and it takes part in nothing afterwards (slot kept).
+ * k_rec = 0 switches C5 off.  Needs LTPC_PAIR_KEY (removals break the
+ * grouping of storage by cell that the bijection mode relies on).
+ * Errors: EINVAL. */
+int ltpc_set_recombination(ltpc_ctx* ctx, double k_rec, double de_rec);
+
 /* Step S1 only: Takizuka-Abe Coulomb collisions (Sec. 4.4) with time step
  * dt (cell j uses dt * dt_factor[j]) at step number `step` (0 <= step <
  * 2^32), then the moments.  Asynchronous. */

@@ -285,12 +285,15 @@ def push(st: State, accel: np.ndarray, dx: float, boundary: int = BOUNDARY_PERIO
     return int(gone.value)
 
 
-def recombine(st: State, params: Params, step: int, k_rec: float, de_rec: float) -> int:
-    """Recombination C5 (RS0-RS5) on the oracle state after the neutral step of `step`;
-    returns how many primaries were removed."""
+def recombine(st: State, params: Params, step: int, k_rec: float, de_rec: float, n_start: int | None = None) -> int:
+    """Recombination C5 (RS0-RS5) on the oracle state after the neutral step of `step`, over the
+    particles present at the start of the step (`n_start`, default all: the secondaries the
+    neutral step appended are not in this step's pairing order); returns how many primaries
+    were removed."""
     gone = C.c_int64(0)
     ids = getattr(st, "ids", None)
-    _check(lib().orc_recombine(st.n, st.M, _p(st.cell, C.c_int32), _p(ids, C.c_uint32), _p(st.vx, C.c_double),
+    n0 = st.n if n_start is None else int(n_start)
+    _check(lib().orc_recombine(n0, st.M, _p(st.cell, C.c_int32), _p(ids, C.c_uint32), _p(st.vx, C.c_double),
                                _p(st.vy, C.c_double), _p(st.vz, C.c_double), _p(st.inv_vol, C.c_double),
                                _p(st.dt, C.c_double), C.byref(params), step, float(k_rec), float(de_rec),
                                C.byref(gone)))

@@ -522,6 +522,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     __shared__ uint32_t s_hist[4 * NBIN];           // four sub-histograms (less atomic contention)
     __shared__ uint32_t s_cmask[CAPL / 32];         // candidate / work bit masks over local positions
     __shared__ uint32_t s_imask[CAPL / 32];         // ionizing positions
+    __shared__ uint32_t s_dmask[CAPL / 32];         // positions of primaries removed by recombination
     __shared__ uint32_t s_ioff[CAPL / 32];          // ionizations before each mask word
     __shared__ uint32_t s_list[LISTCAP];
     __shared__ uint32_t s_misc[4];
@@ -538,6 +539,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     const bool do_coul = (a.flags & F_COULOMB) != 0u;
     const bool do_neut = (a.flags & F_NEUTRAL) != 0u;
     const bool do_corr = (a.flags & F_CORRECTION) != 0u;
+    const bool do_rec = (a.flags & F_RECOMB) != 0u;
 
     // Work items are taken one ahead: while a cell is processed, the next
     // ticket is drawn and its item copied into s_item asynchronously.
@@ -591,7 +593,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // ---- 1a. zero this CTA's bucket counters and histogram
         for (uint32_t i = tid; i <= (SB ? n : nbl); i += NT) bcnt[i] = 0u;   // (SB: n + 1 words)
         for (uint32_t i = tid; i < 4u * NBIN; i += NT) s_hist[i] = 0u;
-        for (uint32_t i = tid; i < CAPL / 32u; i += NT) s_imask[i] = 0u;
+        for (uint32_t i = tid; i < CAPL / 32u; i += NT) { s_imask[i] = 0u; s_dmask[i] = 0u; }
         if (tid == 0) s_vmax = 0u;
         Cl<C>::sync();
 
@@ -1170,13 +1172,61 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 });
                 __syncthreads();   // the primaries' new velocities before the sums below
             }
+            // ---- 5b. recombination C5 (Table 4): RS0, the n_rec primaries of the cell (formed
+            // with its record) are its last pairing positions; RS1-RS3, the r-th takes the
+            // catalyte n_rec positions before it; RS4, the catalyte takes both kinetic energies
+            // and the released one in an isotropic direction (its RECOMB block); RS5, the
+            // primary is removed (cell -1, out of the sums below).  Positions may belong to
+            // other CTAs of a cluster; rank 0 serves every pair.
+            uint32_t n_rec = 0u;
+            if (do_rec && n >= 2u) n_rec = reinterpret_cast<const uint32_t*>(s_cp + CP_BIJ)[CPB_NREC];
+            if (n_rec > 0u) {                                 // uniform over the cluster
+                Cl<C>::sync();                                // every CTA's velocities after C1/C2
+                if (r == 0) {
+                    const T de = a.c_de_rec;
+                    for (uint32_t rr = tid; rr < n_rec; rr += NT) {
+                        const uint32_t qp = n - n_rec + rr, qc = n - 2u * n_rec + rr;
+                        uint32_t b_p, b_c;
+                        const uint32_t op = PB.locate(qp, b_p), oc = PB.locate(qc, b_c);
+                        const uint32_t kp = qp - b_p, kc = qc - b_c;
+                        const T px = *Cl<C>::at(svx + kp, op), py = *Cl<C>::at(svy + kp, op),
+                                pz = *Cl<C>::at(svz + kp, op);
+                        const T cx2 = *Cl<C>::at(svx + kc, oc), cy2 = *Cl<C>::at(svy + kc, oc),
+                                cz2 = *Cl<C>::at(svz + kc, oc);
+                        const uint32_t lp = *Cl<C>::at(sl + kp, op), lc = *Cl<C>::at(sl + kc, oc);
+                        const T Ep = (px * px + py * py + pz * pz) * half_m_over_e;
+                        const T Ec = (cx2 * cx2 + cy2 * cy2 + cz2 * cz2) * half_m_over_e;
+                        const T sp = M::sqrt(two_e_over_m * (Ec + Ep + de));
+                        const uint4 wr = draw(a.keys, lc, step, TAG_RECOMB);
+                        T dx, dy, dz;
+                        iso_dir<T>(wr.x, wr.y, dx, dy, dz);
+                        *Cl<C>::at(svx + kc, oc) = sp * dx;
+                        *Cl<C>::at(svy + kc, oc) = sp * dy;
+                        *Cl<C>::at(svz + kc, oc) = sp * dz;
+                        atomicOr(Cl<C>::at(&s_dmask[kp >> 5], op), 1u << (kp & 31u));
+                        a.cell[lp] = -1;
+                    }
+                }
+                Cl<C>::sync();
+            }
             for (uint32_t p = tid; 2u * p < nloc; p += NT) {
                 const uint32_t ia = 2u * p;
                 const V2 X = *reinterpret_cast<const V2*>(svx + ia);
                 const V2 Y = *reinterpret_cast<const V2*>(svy + ia);
                 const V2 Z = *reinterpret_cast<const V2*>(svz + ia);
-                if (ia + 1u < nloc) accum2(X, Y, Z);
-                else accum(X.x, Y.x, Z.x);
+                if (n_rec == 0u) {
+                    if (ia + 1u < nloc) accum2(X, Y, Z);
+                    else accum(X.x, Y.x, Z.x);
+                } else {                                      // skip the removed primaries
+                    const bool live0 = !((s_dmask[ia >> 5] >> (ia & 31u)) & 1u);
+                    const bool live1 = ia + 1u < nloc && !((s_dmask[(ia + 1u) >> 5] >> ((ia + 1u) & 31u)) & 1u);
+                    if (live0 && live1) {
+                        accum2(X, Y, Z);
+                    } else {
+                        if (live0) accum(X.x, Y.x, Z.x);
+                        if (live1) accum(X.y, Y.y, Z.y);
+                    }
+                }
             }
             T acc[8];
 #pragma unroll
@@ -1191,8 +1241,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 a.hist[(size_t)j * NBIN + tid] = h;
             }
             if (r == 0 && tid == 0) {
+                a.rec_count[j] = n_rec;
+                if (n_rec) atomicOr(&ds->ungroup, 1u);
                 double* m = a.mom + (size_t)j * NMOM;
-                const double N = (double)(n + s_misc[3]);
+                const double N = (double)(n + s_misc[3] - n_rec);
                 m[0] = N;
                 m[1] = a.weight * N;
                 m[2] = s_tot[0]; m[3] = s_tot[1]; m[4] = s_tot[2];

@@ -105,6 +105,16 @@ __device__ void cell_params(const CellParamArgs& cp, int32_t j, double dt, uint3
     f[7] = 0.0f;
     uint32_t* w = reinterpret_cast<uint32_t*>(o + CP_BIJ);
     for (int q = 0; q < CPB_WORDS; ++q) w[q] = 0u;
+    if (cp.k_rec > 0.0 && n >= 2u) {
+        // C5 primaries: floor(P_rec N + U), P_rec = 1 - exp(-dt k_rec n^2), at most N / 2 (the
+        // products in the reference's order, without contraction)
+        const double nj = __dmul_rn(__dmul_rn(cp.weight, (double)n), cp.inv_vol[j]);
+        const double prec = -expm1(-__dmul_rn(__dmul_rn(__dmul_rn(dtj, cp.k_rec), nj), nj));
+        const uint4 wr = philox4x32_10((uint32_t)j, step, TAG_RECOMB, 0u, cp.keys);
+        const double t = floor(__dadd_rn(__dmul_rn(prec, (double)n), fma((double)wr.x, 0x1p-32, 0x1p-33)));
+        const uint32_t cap = n / 2u;
+        w[CPB_NREC] = t <= 0.0 ? 0u : (t >= (double)cap ? cap : (uint32_t)t);
+    }
     if (cp.bijection && n >= BIJ_MIN_N && n <= BIJ_MAX_N) {
         uint32_t a, b, mb;
         bij_shape(n, &a, &b, &mb);
@@ -268,19 +278,24 @@ k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_
             cs_prev[c] = cell_start[c];
             if (appended) counts[c] += ion_count[c];
             ion_count[c] = 0u;
+            counts[c] -= lists.rec_count[c];           // primaries removed by recombination
+            lists.rec_count[c] = 0u;
         }
         if (tid == 0) { ion_off[M] = tot; cs_prev[M] = cell_start[M]; }
         total_ion = appended ? tot : 0u;
         __syncthreads();
     }
 
-    // 2. CCS2: offsets of the grouping
+    // 2. CCS2: offsets of the grouping.  After a pass that removed particles the cells are no
+    // longer runs of the storage: every particle takes its place from the cursor from now on.
     {
+        const bool ungroup = ds->ungroup != 0u;
         uint32_t sum = 0u;
         for (uint32_t c = b0; c < b1; ++c) sum += counts[c];
         uint32_t tot;
         uint32_t ex = block_scan(sum, &tot);
         for (uint32_t c = b0; c < b1; ++c) {
+            if (ungroup) lists.run_len[c] = 0u;
             cell_start[c] = ex;
             cursor[c] = ex + lists.run_len[c];   // appended particles follow the cell's run
             ex += counts[c];
@@ -344,10 +359,16 @@ k_regroup(int32_t M, uint32_t* __restrict__ counts, uint32_t* __restrict__ cell_
     }
     __syncthreads();
     if (tid == 0) {
+        const bool ug = ds->ungroup != 0u;
+        if (ug) {
+            ds->n_sorted = 0ull;
+            ds->n_loaded = ~0ull;
+            ds->ungroup = 0u;
+        }
         ds->max_count = s_max;
         ds->n_ion = total_ion;
-        // after a pass that appended nothing the grouping of the next pass is this one's
-        ds->grouping_valid = (lists.cache_grouping && append && total_ion == 0u) ? 1u : 0u;
+        // after a pass that appended and removed nothing the grouping of the next pass is this one's
+        ds->grouping_valid = (lists.cache_grouping && append && total_ion == 0u && !ug) ? 1u : 0u;
         ds->n += total_ion;
         if (advance_step) ds->step += 1u;
     }

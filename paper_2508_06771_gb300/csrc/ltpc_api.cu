@@ -31,7 +31,7 @@ struct Layout {
     size_t vx, vy, vz, cell, x;
     // work offsets
     size_t perm, counts, cell_start, cs_prev, cursor, ion_count, ion_off, stage_l, stage_vx, stage_vy,
-        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, accel, lists, ds;
+        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, accel, rec_count, lists, ds;
 };
 
 bool compute_layout(const ltpc_config* c, Layout* L)
@@ -70,6 +70,7 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->run_len = take(M * 4);
     L->aslot = take(cap * 4);
     L->accel = take(M * 8);
+    L->rec_count = take(M * 4);
     L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
     L->work = o;
@@ -105,6 +106,8 @@ struct ltpc_ctx {
     bool field = false;
     double dx = 0.0;
     int32_t wall = LTPC_WALL_PERIODIC;
+    // recombination C5 (ltpc_set_recombination)
+    double k_rec = 0.0, de_rec = 0.0;
     char cuda_err[256] = {0};
 
     template <class P> P* w(size_t off) const { return reinterpret_cast<P*>(wk + off); }
@@ -139,6 +142,7 @@ int set_table(ltpc_ctx* ctx, int table)
     ctx->lists.run_start = ctx->w<uint32_t>(ctx->L.run_start);
     ctx->lists.run_len = ctx->w<uint32_t>(ctx->L.run_len);
     ctx->lists.aslot = ctx->w<uint32_t>(ctx->L.aslot);
+    ctx->lists.rec_count = ctx->w<uint32_t>(ctx->L.rec_count);
     for (int k = 0; k < MAX_CLASSES; ++k) {
         ctx->lists.max_n[k] = 0;
         ctx->lists.list[k] = ctx->w<uint4>(ctx->L.lists) + (size_t)k * ctx->cfg.n_cells;
@@ -194,6 +198,9 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.c_nsig_tot = (T)(ctx->cfg.n_neutral * (ctx->cfg.sigma_el + ctx->cfg.sigma_ion));
     a.c_e_ion = (T)ctx->cfg.e_ion;
     a.c_mratio2 = (T)a.mratio2;
+    a.cell = ctx->s<int32_t>(L.cell);
+    a.rec_count = ctx->w<uint32_t>(L.rec_count);
+    a.c_de_rec = (T)ctx->de_rec;
     a.run_start = ctx->w<uint32_t>(L.run_start);
     a.run_len = ctx->w<uint32_t>(L.run_len);
     a.order_out = nullptr;
@@ -251,6 +258,7 @@ int enqueue_body(ltpc_ctx* ctx, uint32_t flags, bool advance, uint32_t* order_ou
     cp.e_over_m = ctx->cfg.charge / ctx->cfg.mass;
     cp.lnl_nrl = ctx->cfg.lnlambda_mode == LTPC_LNL_NRL ? 1 : 0;
     cp.bijection = ctx->cfg.pairing_mode == LTPC_PAIR_BIJECTION ? 1 : 0;
+    cp.k_rec = (flags & F_RECOMB) ? ctx->k_rec : 0.0;
     cp.keys = philox_keys(ctx->cfg.seed);
     CK(launch_scatter(ctx->s<int32_t>(L.cell), ctx->cfg.n_cells, ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
                       grid_stream, s, ctx->lists, ctx->w<uint32_t>(L.cell_start), &cp));
@@ -304,6 +312,7 @@ uint32_t step_flags(const ltpc_ctx* ctx, bool coulomb, bool neutral)
         if (ctx->cfg.lnlambda_mode == LTPC_LNL_NRL) f |= F_LNL_NRL;
     }
     if (neutral && ctx->cfg.n_neutral > 0.0) f |= F_NEUTRAL;
+    if (neutral && ctx->k_rec > 0.0) f |= F_RECOMB;
     if (ctx->field) f |= F_PUSH;
     return f;
 }
@@ -534,6 +543,17 @@ int ltpc_set_field(ltpc_ctx* ctx, double dx, const double* accel, int32_t bounda
     ctx->field = true;
     ctx->dx = dx;
     ctx->wall = boundary;
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    return LTPC_OK;
+}
+
+int ltpc_set_recombination(ltpc_ctx* ctx, double k_rec, double de_rec)
+{
+    if (!ctx || !(k_rec >= 0.0) || !std::isfinite(k_rec) || !(de_rec >= 0.0) || !std::isfinite(de_rec))
+        return LTPC_EINVAL;
+    if (k_rec > 0.0 && ctx->cfg.pairing_mode != LTPC_PAIR_KEY) return LTPC_EINVAL;
+    ctx->k_rec = k_rec;
+    ctx->de_rec = de_rec;
     if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
     return LTPC_OK;
 }

@@ -25,6 +25,7 @@ enum : uint32_t {
     F_CORRECTION = 4u,       // restore per-cell momentum and energy after S1
     F_LNL_NRL = 8u,          // Coulomb logarithm from the cell's previous moments
     F_PUSH = 16u,            // host only: the pass ends with steps S2b/S2c (a field is set)
+    F_RECOMB = 32u,          // recombination C5 after the electron-neutral collisions
 };
 
 constexpr int MAX_CLASSES = 8;
@@ -47,6 +48,7 @@ struct DevState {
     unsigned long long n_sorted;      // particles [0, n_sorted) lie in per-cell runs (cell-grouped load)
     unsigned long long n_loaded;      // particles [n_loaded, n) were appended: each has its slot in its
                                       // cell's grouping (RegroupLists::aslot)
+    unsigned int ungroup;             // 1: a pass removed particles; the next regrouping drops the runs
 };
 
 // Per-cell scalars of one pass, formed by a grid-wide loop at the start of
@@ -71,6 +73,7 @@ enum : int {
     CPB_MB = 1,      // ceil(2^32 / b)
     CPB_KEY = 2,     // 2..7: the six round keys
     CPB_U = 8,       // candidate-count rounding word
+    CPB_NREC = 9,    // recombination C5: primaries of the cell this pass (0 when off)
     CPB_WORDS = 10
 };
 struct CellParamArgs {
@@ -84,6 +87,7 @@ struct CellParamArgs {
     int lnl_nrl;                 // 1: Coulomb logarithm by the NRL e-e formula
     int bijection;               // 1: cells of BIJ_MIN_N..BIJ_MAX_N particles are paired by the bijection
     PhiloxKeys keys;             // round keys of the seed (the bijection's round keys are drawn per cell)
+    double k_rec;                // three-body recombination rate [m^6/s] (0: no C5)
 };
 
 // Arguments of the cell kernel (one cluster per cell).
@@ -115,6 +119,9 @@ struct CellArgs {
     T c_nsig_el, c_nsig_ion;     // n_n sigma_el, n_n sigma_ion
     T c_nsig_tot;                // n_n (sigma_el + sigma_ion), rounded once
     T c_e_ion, c_mratio2;
+    int32_t* cell;               // cell id of every particle (C5 marks removed primaries with -1)
+    uint32_t* rec_count;         // [M] primaries removed by this pass (C5)
+    T c_de_rec;                  // energy released to the catalyte [eV]
     const uint32_t* run_start;   // [M] first index of each cell's loaded run (storage grouped by cell)
     const uint32_t* run_len;     // [M] its length (0: not grouped)
     uint32_t* order_out;         // optional: pairing order written at I_j + position

@@ -26,6 +26,7 @@ struct RegroupLists {
     // secondaries of the cell.  The scatter places appended particles there
     // without atomics, after the loaded ones, in ascending index order.
     uint32_t* aslot;
+    uint32_t* rec_count;           // [M] primaries removed by the last pass (recombination C5)
 };
 
 // One compiled shape of the cell kernel.

@@ -12,7 +12,8 @@
 
 namespace ltpc {
 
-enum : uint32_t { TAG_PARTICLE = 1u, TAG_PAIR = 2u, TAG_SCATTER = 3u, TAG_SECONDARY = 4u, TAG_PERM = 5u };
+enum : uint32_t { TAG_PARTICLE = 1u, TAG_PAIR = 2u, TAG_SCATTER = 3u, TAG_SECONDARY = 4u, TAG_PERM = 5u,
+                  TAG_RECOMB = 6u };
 
 __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                                uint32_t k0, uint32_t k1)

@@ -68,6 +68,7 @@ def load_library(path: str = LIB_PATH):
             "ltpc_load_particles": (C.c_int, [vp, i64, vp, vp, vp, vp, vp, C.c_int]),
             "ltpc_set_field": (C.c_int, [vp, C.c_double, vp, i32]),
             "ltpc_push": (C.c_int, [vp, C.c_double, i64]),
+            "ltpc_set_recombination": (C.c_int, [vp, C.c_double, C.c_double]),
             "ltpc_collide_coulomb": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_collide_neutral": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_step": (C.c_int, [vp, C.c_double, i64]),
@@ -218,6 +219,10 @@ class Collider:
         """Steps S2b/S2c: cells of width dx along z, per-cell acceleration accel [M] (m/s^2)."""
         self._accel = np.ascontiguousarray(accel, dtype=np.float64)
         self._check(self.L.ltpc_set_field(self.ctx, float(dx), self._accel.ctypes.data, int(boundary)), "set_field")
+
+    def set_recombination(self, k_rec: float, de_rec: float):
+        """Recombination C5: three-body rate k_rec [m^6/s], energy de_rec [eV] to the catalyte."""
+        self._check(self.L.ltpc_set_recombination(self.ctx, float(k_rec), float(de_rec)), "set_recombination")
 
     def push(self, dt, step):
         self._check(self.L.ltpc_push(self.ctx, float(dt), int(step)), "push")
