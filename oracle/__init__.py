@@ -55,8 +55,22 @@ class Params(C.Structure):
         ("weight", C.c_double), ("n_neutral", C.c_double), ("mass_neutral", C.c_double),
         ("sigma_el", C.c_double), ("sigma_ion", C.c_double), ("e_ion", C.c_double),
         ("seed", C.c_uint64), ("odd_mode", C.c_int32), ("correction", C.c_int32),
-        ("pairing_mode", C.c_int32), ("reserved", C.c_int32), ("cell_ids", C.c_void_p),
+        ("pairing_mode", C.c_int32), ("selection", C.c_int32), ("cell_ids", C.c_void_p),
+        ("xs_el", C.c_void_p), ("xs_ion", C.c_void_p), ("sigma_max", C.c_double),
     ]
+
+
+class Xs(C.Structure):
+    """A tabulated cross section (orc_xs): piecewise cubic on a uniform ln E grid."""
+    _fields_ = [("pieces", C.c_int32), ("zero_below", C.c_int32), ("lnE0", C.c_double), ("h", C.c_double),
+                ("coef", C.c_void_p)]
+
+
+def _xs(table):
+    coef = np.ascontiguousarray(table["coef"], dtype=np.float64)
+    x = Xs(int(table["pieces"]), int(table["zero_below"]), float(table["lnE0"]), float(table["h"]), coef.ctypes.data)
+    x._coef = coef
+    return x
 
 
 def _p(a, ct):
@@ -102,6 +116,8 @@ def lib():
             L.orc_recombine.argtypes = [C.c_int64, C.c_int32, i32p, u32p, f64p, f64p, f64p, f64p, f64p,
                                         C.POINTER(Params), C.c_uint32, C.c_double, C.c_double, i64p]
             L.orc_bin.argtypes = [C.c_double, C.c_double, C.c_int32]
+            L.orc_xs_eval.argtypes = [C.c_void_p, C.c_double]
+            L.orc_xs_eval.restype = C.c_double
             L.orc_bin.restype = C.c_int
             L.orc_pair_order_mode.argtypes = [C.c_int64, C.c_int32, i32p, u32p, C.POINTER(Params), C.c_uint32,
                                               u64p, u32p]
@@ -187,7 +203,13 @@ def make_params(cfg: dict, correction: bool = False, pairing_mode: int | None = 
     P = Params(cfg["mass"], cfg["charge"], cfg["eps0"], cfg["weight"],
                cfg.get("n_neutral", 0.0), cfg.get("mass_neutral", 1.0),
                cfg.get("sigma_el", 0.0), cfg.get("sigma_ion", 0.0), cfg.get("e_ion", 1e30),
-               int(cfg["seed"]), int(cfg.get("odd_mode", 0)), 1 if correction else 0, mode, 0, None)
+               int(cfg["seed"]), int(cfg.get("odd_mode", 0)), 1 if correction else 0, mode,
+               int(cfg.get("selection", 0)), None, None, None, 0.0)
+    xs = cfg.get("xs")                  # (elastic table, ionization table, bound on their sum)
+    if xs is not None:
+        P._xs = (_xs(xs[0]), _xs(xs[1]))
+        P.xs_el, P.xs_ion = C.addressof(P._xs[0]), C.addressof(P._xs[1])
+        P.sigma_max = float(xs[2])
     cid = cfg.get("cell_ids")
     if cid is not None:
         P._cell_ids = np.ascontiguousarray(cid, dtype=np.uint32)    # kept alive with the struct
@@ -298,6 +320,12 @@ def recombine(st: State, params: Params, step: int, k_rec: float, de_rec: float,
                                _p(st.dt, C.c_double), C.byref(params), step, float(k_rec), float(de_rec),
                                C.byref(gone)))
     return int(gone.value)
+
+
+def xs_eval(table: dict, E: float) -> float:
+    """The oracle's value of a tabulated cross section at E [eV]."""
+    x = _xs(table)
+    return lib().orc_xs_eval(C.addressof(x), float(E))
 
 
 def bin_position(x: float, dx: float, M: int) -> int:

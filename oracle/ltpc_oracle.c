@@ -52,6 +52,18 @@ enum { ORC_PAIR_KEY = 0, ORC_PAIR_BIJECTION = 1 };
 /* Error codes (same numeric meaning as the library's, defined independently). */
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ECAPACITY = -2 };
 
+/* A cross section as a piecewise cubic in ln E (Sec. 4.2 replaces the
+ * table lookup with a piecewise polynomial interpolation): interval i of the
+ * uniform grid ln E0 + [i, i+1) h holds c0 + c1 t + c2 t^2 + c3 t^3 with
+ * t = (ln E - ln E0)/h - i; below E0 the value is 0 (zero_below) or the
+ * first knot's; above the last knot, the last knot's. */
+typedef struct {
+    int32_t pieces;
+    int32_t zero_below;
+    double lnE0, h;
+    const double *coef;  /* [pieces][4] */
+} orc_xs;
+
 typedef struct {
     double mass;         /* electron mass m [kg]                         */
     double charge;       /* elementary charge e [C]                      */
@@ -66,9 +78,34 @@ typedef struct {
     int32_t odd_mode;    /* 0: last particle of an odd cell sits out     */
     int32_t correction;  /* 1: restore per-cell momentum+energy after TA */
     int32_t pairing_mode;/* ORC_PAIR_KEY or ORC_PAIR_BIJECTION           */
-    int32_t reserved;
+    int32_t selection;   /* 0 null collision, 1 per-particle probabilities */
     const uint32_t *cell_ids; /* random-stream id of each cell (NULL: its index) */
+    const orc_xs *xs_el, *xs_ion; /* tabulated cross sections (NULL: the constant / step ones) */
+    double sigma_max;    /* bound on sigma_el + sigma_ion with the tables */
 } orc_params;
+
+double orc_xs_eval(const orc_xs *t, double E)
+{
+    if (!(E > 0.0)) return t->zero_below ? 0.0 : t->coef[0];
+    double u = (log(E) - t->lnE0) / t->h;
+    if (u < 0.0) return t->zero_below ? 0.0 : t->coef[0];
+    double fi = floor(u);
+    int32_t i = (int32_t)fi;
+    double x;
+    if (i >= t->pieces) { i = t->pieces - 1; x = 1.0; }
+    else x = u - fi;
+    const double *c = t->coef + 4 * (size_t)i;
+    return c[0] + x * (c[1] + x * (c[2] + x * c[3]));
+}
+
+/* sigma_el(E), sigma_ion(E): the tables when given, else the constant elastic and
+ * the step ionization cross sections. */
+static double orc_sig_el(const orc_params *p, double E) { return p->xs_el ? orc_xs_eval(p->xs_el, E) : p->sigma_el; }
+static double orc_sig_ion(const orc_params *p, double E)
+{
+    if (p->xs_ion) return orc_xs_eval(p->xs_ion, E);
+    return E >= p->e_ion ? p->sigma_ion : 0.0;
+}
 
 /* ------------------------------------------------------------------------- *
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random numbers:
@@ -578,8 +615,11 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
         double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
         if (v2 > vmax2[cell[l]]) vmax2[cell[l]] = v2;
     }
-    const double sig_tot = p->sigma_el + p->sigma_ion;
+    /* nu_max = n_n sigma_max v_max: sigma_max = sigma_el + sigma_ion for the
+     * constant / step cross sections, the given bound with tables */
+    const double sig_tot = (p->xs_el || p->xs_ion) ? p->sigma_max : p->sigma_el + p->sigma_ion;
     const double e_over_m = p->charge / p->mass;
+    const int per_particle = p->selection == 1;
     /* Bijection mode, cells of at least ORC_BIJ_MIN_N particles: the paper
      * selects P_null N particles at random (Sec. 4.2).  Reading: the count is
      * n_c = floor(P_null N + U) with U the cell's candidate-count uniform
@@ -588,7 +628,7 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
      * (a uniformly random subset, since the positions are a keyed bijection
      * of the id ranks).  cmarg: distance of P_null N + U to the nearest
      * integer relative to P_null N (for the two particles next to the cut). */
-    if (bij) {
+    if (bij && !per_particle) {
         int rc0 = orc_pair_order_mode(n, M, cell, ids, p, step, bcs, bord);
         if (rc0) {
             free(vmax2); free(nion); free(ionize); free(sec); free(cand); free(cmarg); free(bcs); free(bord);
@@ -623,6 +663,50 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
         orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_PARTICLE, w);
         double uc = orc_uniform(w[1]);
         int is_cand;
+        if (per_particle) {
+            /* Sec. 4.2's per-particle selection: pi_c = 1 - exp(-dt v sigma_c(v) n_n) for
+             * each collision c, decided by U1 against pi_el, pi_el + pi_ion (reading: one
+             * uniform, collisions in the order of Table 1) */
+            double v2p = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
+            double vp_ = sqrt(v2p), Ep_ = 0.5 * v2p / e_over_m;
+            double pel = -expm1(-dt[j] * vp_ * orc_sig_el(p, Ep_) * p->n_neutral);
+            double pio = -expm1(-dt[j] * vp_ * orc_sig_ion(p, Ep_) * p->n_neutral);
+            int kind = uc < pel ? 2 : (uc < pel + pio ? 3 : 0);
+            if (margin) {
+                double mm = fmin(fabs(uc - pel), fabs(uc - pel - pio));
+                if (p->xs_ion == NULL && p->sigma_ion > 0.0) mm = fmin(mm, fabs(Ep_ - p->e_ion) / p->e_ion);
+                margin[l] = mm;
+            }
+            if (decision) decision[l] = (int8_t)kind;
+            if (kind == 0) continue;
+            ++ncand;
+            uint32_t s_[4];
+            orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_SCATTER, s_);
+            double d_[3];
+            orc_iso_dir(s_[0], s_[1], d_);
+            if (kind == 2) {
+                ++nel;
+                double cchi = (vx[l] * d_[0] + vy[l] * d_[1] + vz[l] * d_[2]) / vp_;
+                double f = 1.0 - 2.0 * (p->mass / p->mass_neutral) * (1.0 - cchi);
+                double vn = vp_ * sqrt(f);
+                vx[l] = vn * d_[0]; vy[l] = vn * d_[1]; vz[l] = vn * d_[2];
+            } else {
+                ++nio;
+                double Ep = fmax(Ep_ - p->e_ion, 0.0);
+                double Es = orc_uniform(s_[2]) * Ep;
+                double Eprim = Ep - Es;
+                double vpr = sqrt(2.0 * Eprim * e_over_m), vs = sqrt(2.0 * Es * e_over_m);
+                uint32_t t_[4];
+                orc_draw(p->seed, orc_id(ids, (uint64_t)l), step, ORC_TAG_SECONDARY, t_);
+                double ds_[3];
+                orc_iso_dir(t_[0], t_[1], ds_);
+                vx[l] = vpr * d_[0]; vy[l] = vpr * d_[1]; vz[l] = vpr * d_[2];
+                sec[3 * l + 0] = vs * ds_[0]; sec[3 * l + 1] = vs * ds_[1]; sec[3 * l + 2] = vs * ds_[2];
+                ionize[l] = 1;
+                nion[j] += 1;
+            }
+            continue;
+        }
         if (bij && cand[l] != 0) {                 /* cell paired by the bijection */
             is_cand = cand[l] > 0;
             if (margin) margin[l] = cmarg[l];
@@ -635,14 +719,14 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
         double v2 = vx[l] * vx[l] + vy[l] * vy[l] + vz[l] * vz[l];
         double v = sqrt(v2);
         double E = 0.5 * v2 / e_over_m;                           /* eV */
-        double nu_el = p->n_neutral * p->sigma_el * v;
-        double nu_ion = E >= p->e_ion ? p->n_neutral * p->sigma_ion * v : 0.0;
+        double nu_el = p->n_neutral * orc_sig_el(p, E) * v;
+        double nu_ion = p->n_neutral * orc_sig_ion(p, E) * v;
         double r = orc_uniform(w[2]) * numax;
         int kind = r < nu_el ? 2 : (r < nu_el + nu_ion ? 3 : 1);
         if (decision) decision[l] = (int8_t)kind;
         if (margin && numax > 0.0) {
             double m1 = fabs(r - nu_el) / numax, m2 = fabs(r - nu_el - nu_ion) / numax;
-            double me = p->sigma_ion > 0.0 ? fabs(E - p->e_ion) / p->e_ion : 1.0;
+            double me = (p->xs_ion == NULL && p->sigma_ion > 0.0) ? fabs(E - p->e_ion) / p->e_ion : 1.0;
             double mm = margin[l];
             if (m1 < mm) mm = m1;
             if (m2 < mm) mm = m2;
@@ -662,7 +746,7 @@ int orc_neutral_ids(int64_t *n_io, int64_t capacity, int32_t M, int32_t *cell, c
             vx[l] = vn * d[0]; vy[l] = vn * d[1]; vz[l] = vn * d[2];
         } else {
             ++nio;
-            double Ep = E - p->e_ion;
+            double Ep = fmax(E - p->e_ion, 0.0);
             double Es = orc_uniform(s[2]) * Ep;
             double Eprim = Ep - Es;
             double vp = sqrt(2.0 * Eprim * e_over_m), vs = sqrt(2.0 * Es * e_over_m);
@@ -740,8 +824,8 @@ int orc_moments(int64_t n, int32_t M, const int32_t *cell, const double *vx, con
         m[1] += p->weight;
         m[2] += vx[l]; m[3] += vy[l]; m[4] += vz[l];
         m[5] += vx[l] * vx[l]; m[6] += vy[l] * vy[l]; m[7] += vz[l] * vz[l];
-        m[8] += p->sigma_el * v;
-        m[9] += (E >= p->e_ion ? p->sigma_ion : 0.0) * v;
+        m[8] += orc_sig_el(p, E) * v;
+        m[9] += orc_sig_ion(p, E) * v;
         if (hist) hist[64 * (size_t)j + (size_t)orc_energy_bin(E)] += 1;
     }
     return ORC_OK;

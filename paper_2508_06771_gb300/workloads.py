@@ -237,3 +237,57 @@ def subset_cells(wl: dict, cells) -> dict:
     if wl.get("x") is not None:
         out["x"] = wl["x"][keep]
     return out
+
+
+# ----------------------------------------------------------------------------- cross-section tables
+# Sec. 4.2 replaces the LXCat lookup with a piecewise polynomial of each cross
+# section (error under 2 %).  The LXCat argon data are not available, so smooth
+# argon-like stand-ins are tabulated instead: an elastic cross section with a
+# low-energy minimum and a peak near 12 eV, and an ionization cross section of
+# the ln(E/I)/(E/I) form above I = 15.76 eV peaking near 2.9e-20 m^2.  A table is
+# a cubic per interval of a uniform grid in ln E (Hermite: values and slopes at
+# the knots), the layout both the library and the oracle evaluate.
+
+def sigma_el_argon_like(E):
+    """Elastic stand-in [m^2] for E [eV]."""
+    E = np.asarray(E, np.float64)
+    return 1.2e-20 + 1.45e-19 * (E / 12.0) ** 2 / (1.0 + (E / 12.0) ** 2.6) + 4e-21 / (1.0 + E / 0.05)
+
+
+def sigma_ion_argon_like(E):
+    """Ionization stand-in [m^2] for E [eV]: 2.9e-20 e ln(E/I) / (E/I) above I = 15.76 eV."""
+    E = np.asarray(E, np.float64)
+    x = np.maximum(E / E_ION, 1.0)
+    return np.where(E >= E_ION, 2.9e-20 * math.e * np.log(x) / x, 0.0)
+
+
+def xsec_table(f, e_lo, e_hi, pieces, zero_below):
+    """Piecewise cubic Hermite table of f on a uniform ln E grid [e_lo, e_hi]: a dict with
+    lnE0, h, pieces, zero_below and coef [pieces, 4] (sigma = c0 + c1 t + c2 t^2 + c3 t^3,
+    t = (ln E - lnE0)/h - i in interval i)."""
+    lnE = np.linspace(math.log(e_lo), math.log(e_hi), pieces + 1)
+    h = lnE[1] - lnE[0]
+    E = np.exp(lnE)
+    y = f(E)
+    # slopes d sigma / d lnE by a centred difference of the function itself
+    eps = 1e-5
+    d = (f(E * math.exp(eps)) - f(E * math.exp(-eps))) / (2 * eps)
+    if zero_below:
+        d[0] = (f(E[0] * math.exp(eps)) - y[0]) / eps     # one-sided at the threshold
+    coef = np.zeros((pieces, 4))
+    for i in range(pieces):
+        y0, y1, m0, m1 = y[i], y[i + 1], d[i] * h, d[i + 1] * h
+        coef[i] = [y0, m0, 3 * (y1 - y0) - 2 * m0 - m1, 2 * (y0 - y1) + m0 + m1]
+    return {"lnE0": float(lnE[0]), "h": float(h), "pieces": int(pieces), "zero_below": int(zero_below),
+            "coef": coef}
+
+
+def argon_like_tables(pieces_el=64, pieces_ion=48):
+    """The elastic table on [0.01, 1000] eV, the ionization one on [I, 1000] eV, and a bound
+    on sigma_el + sigma_ion over all energies (2 % over the largest of a dense sampling; the
+    null-collision bound uses it)."""
+    el = xsec_table(sigma_el_argon_like, 1e-2, 1e3, pieces_el, zero_below=False)
+    ion = xsec_table(sigma_ion_argon_like, E_ION, 1e3, pieces_ion, zero_below=True)
+    E = np.exp(np.linspace(math.log(1e-3), math.log(1e4), 200001))
+    smax = 1.02 * float(np.max(sigma_el_argon_like(E) + sigma_ion_argon_like(E)))
+    return el, ion, smax
