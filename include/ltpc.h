@@ -187,6 +187,46 @@ int ltpc_push(ltpc_ctx* ctx, double dt, int64_t step);
  * Errors: EINVAL. */
 int ltpc_set_recombination(ltpc_ctx* ctx, double k_rec, double de_rec);
 
+/* ---- tabulated cross sections and per-particle selection (Sec. 4.2) ------
+ * The paper evaluates each electron-neutral cross section as a piecewise
+ * polynomial fit in place of a table lookup.  One table: interval i of the
+ * uniform grid ln E0 + [i, i+1) h (E in eV) holds the cubic
+ * c0 + c1 t + c2 t^2 + c3 t^3 [m^2] in t = (ln E - ln E0)/h - i; below E0 the
+ * value is 0 (zero_below = 1, as an ionization threshold) or c0 of the first
+ * piece (zero_below = 0); above the last knot it is the last piece's value at
+ * t = 1.  coef is a host array [pieces][4], copied by the call. */
+#define LTPC_XS_MAX_PIECES 256
+typedef struct ltpc_xsec {
+    int32_t pieces;             /* 1 .. LTPC_XS_MAX_PIECES                      */
+    int32_t zero_below;         /* 1: 0 below E0; 0: the first knot's value      */
+    double lnE0;                /* ln of the first knot energy (E in eV)        */
+    double h;                   /* knot spacing in ln E, > 0                    */
+    const double* coef;         /* [pieces][4] host, finite                     */
+} ltpc_xsec;
+
+#define LTPC_SELECT_NULL 0          /* null-collision method (Sec. 4.2)          */
+#define LTPC_SELECT_PER_PARTICLE 1  /* per-particle collision probabilities      */
+
+/* sigma_el(E) and sigma_ion(E) of C1/C2 from tables (el or ion NULL: that one
+ * stays the configuration's constant, resp. step at e_ion), used by the
+ * collision decisions of S2a and by the rate sums of the moments (mom 8, 9:
+ * sum sigma(E) |v|).  sigma_max [m^2] bounds sigma_el(E) + sigma_ion(E) for
+ * every E: the null-collision frequency is nu_max = n_n sigma_max v_max (with
+ * both tables NULL it stays n_n (sigma_el + sigma_ion) v_max).  selection:
+ * LTPC_SELECT_NULL, or LTPC_SELECT_PER_PARTICLE, where every particle collides
+ * with probabilities pi_c = 1 - exp(-dt_j v sigma_c(E) n_n), decided by one
+ * uniform U1 of its PARTICLE block against pi_el and pi_el + pi_ion (C1 first,
+ * Table 1's order); needs LTPC_PAIR_KEY.  Both tables NULL with
+ * LTPC_SELECT_NULL restores the constant cross sections.  The ionization
+ * outcome keeps E - e_ion as the energy shared by the two electrons.  binary64
+ * evaluates the tables with the natural logarithm, one division and Horner's
+ * rule; binary32 with the fast hardware logarithm and binary32 coefficients
+ * (relative error near 1e-6).  The call samples each table (32 points per
+ * piece and the knots) and rejects a negative value or a sum above sigma_max.
+ * Synchronizing.  Errors: EINVAL. */
+int ltpc_set_cross_sections(ltpc_ctx* ctx, const ltpc_xsec* el, const ltpc_xsec* ion, double sigma_max,
+                            int32_t selection);
+
 /* Step S1 only: Takizuka-Abe Coulomb collisions (Sec. 4.4) with time step
  * dt (cell j uses dt * dt_factor[j]) at step number `step` (0 <= step <
  * 2^32), then the moments.  Asynchronous. */

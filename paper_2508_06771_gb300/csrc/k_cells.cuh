@@ -1010,7 +1010,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const T dtj = cell_scalar<T>(s_cp, 1);
             auto bound = [&](T md, T& nmx, T& pn, uint32_t& h) {   // null-collision bound of the cell
                 nmx = a.c_nsig_tot * Math<T>::sqrt(md);
-                pn = -Math<T>::expm1(-nmx * dtj);
+                // per-particle selection (tables, key pairing): pi_el + pi_ion <=
+                // dt v (sigma_el + sigma_ion) n_n <= nu_max dt, so U below that bound
+                // (widened past rounding) screens every particle that can collide
+                pn = a.xs.per_particle ? fmin(T(1), nmx * dtj * T(1.0001)) : -Math<T>::expm1(-nmx * dtj);
                 h = cand_threshold<T>(pn);
             };
             if constexpr (C == 1) {
@@ -1045,22 +1048,44 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             auto collide = [&](uint32_t q) {
                 const uint32_t l = sl[q];
                 const uint4 rw = draw(a.keys, l, step, TAG_PARTICLE);
-                if (bij_ab == 0u && !(unif<T>(rw.y) < pnull)) return;
+                const T u1 = unif<T>(rw.y);
+                if (bij_ab == 0u && !(u1 < pnull)) return;
                 const T x = svx[q], y = svy[q], z = svz[q];
                 const T v2 = x * x + y * y + z * z;
                 const T v = Math<T>::sqrt(v2);
                 const T E = v2 * half_m_over_e;
-                const T nu_el = nsel * v;
-                const T nu_ion = E >= e_ion ? nsion * v : T(0);
-                const T rr = unif<T>(rw.z) * numax;
-                if (rr < nu_el) {                              // C1: elastic, cold heavy target
+                bool el, io;
+                if (!a.xs.on) {
+                    const T nu_el = nsel * v;
+                    const T nu_ion = E >= e_ion ? nsion * v : T(0);
+                    const T rr = unif<T>(rw.z) * numax;
+                    el = rr < nu_el;
+                    io = !el && rr < nu_el + nu_ion;
+                } else {
+                    const T sg_el = xs_el<T>(a.xs, E, a.c_sig_el), sg_ion = xs_ion<T>(a.xs, E, a.c_sig_ion, e_ion);
+                    if (a.xs.per_particle) {
+                        // Sec. 4.2: pi_c = 1 - exp(-dt v sigma_c n_n), one uniform against
+                        // pi_el, pi_el + pi_ion
+                        const T pel = -Math<T>::expm1(-dtj * v * sg_el * a.c_nn);
+                        const T pio = -Math<T>::expm1(-dtj * v * sg_ion * a.c_nn);
+                        el = u1 < pel;
+                        io = !el && u1 < pel + pio;
+                    } else {
+                        const T nu_el = a.c_nn * sg_el * v;
+                        const T nu_ion = a.c_nn * sg_ion * v;
+                        const T rr = unif<T>(rw.z) * numax;
+                        el = rr < nu_el;
+                        io = !el && rr < nu_el + nu_ion;
+                    }
+                }
+                if (el) {                                      // C1: elastic, cold heavy target
                     const uint4 sc = draw(a.keys, l, step, TAG_SCATTER);
                     T dx, dy, dz;
                     iso_dir<T>(sc.x, sc.y, dx, dy, dz);
                     const T cchi = (x * dx + y * dy + z * dz) * Math<T>::rcp(v);
                     const T vn = v * Math<T>::sqrt(T(1) - mr2 * (T(1) - cchi));
                     svx[q] = vn * dx; svy[q] = vn * dy; svz[q] = vn * dz;
-                } else if (rr < nu_el + nu_ion) {              // C2: ionization, resolved below
+                } else if (io) {                               // C2: ionization, resolved below
                     atomicOr(&s_imask[q >> 5], 1u << (q & 31u));
                     ionized = true;
                 }
@@ -1118,9 +1143,12 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const T e_ion = a.c_e_ion, two_e_over_m = a.c_two_e_over_m;
             // per-thread sums, two lanes each (positions 2p and 2p+1 of the pair slots):
             // v_x, v_y, v_z, v_x^2, v_y^2, v_z^2, |v|, |v| above the ionization threshold
+            // (with tabulated cross sections: sigma_el(E) |v| and sigma_ion(E) |v|)
             V2 q[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) q[k] = P::make(T(0), T(0));
+            const bool xs_on = a.xs.on != 0;
+            const T sg0 = a.c_sig_el, si0 = a.c_sig_ion;
             uint32_t* hsub = s_hist + ((tid >> 5) & 3u) * NBIN;
             const V2 HM = P::make(half_m_over_e, half_m_over_e);
             auto accum2 = [&](V2 X, V2 Y, V2 Z) {
@@ -1129,8 +1157,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const V2 E = P::mul(v2, HM);
                 P::acc(q[0], X); P::acc(q[1], Y); P::acc(q[2], Z);
                 P::acc_sq(q[3], X); P::acc_sq(q[4], Y); P::acc_sq(q[5], Z);
-                P::acc(q[6], V);
-                P::acc(q[7], P::make(E.x >= e_ion ? V.x : T(0), E.y >= e_ion ? V.y : T(0)));
+                if (!xs_on) {
+                    P::acc(q[6], V);
+                    P::acc(q[7], P::make(E.x >= e_ion ? V.x : T(0), E.y >= e_ion ? V.y : T(0)));
+                } else {                                       // tables: sums of sigma(E) |v|
+                    P::acc(q[6], P::make(xs_el<T>(a.xs, E.x, sg0) * V.x, xs_el<T>(a.xs, E.y, sg0) * V.y));
+                    P::acc(q[7], P::make(xs_ion<T>(a.xs, E.x, si0, e_ion) * V.x, xs_ion<T>(a.xs, E.y, si0, e_ion) * V.y));
+                }
                 atomicAdd(&hsub[M::ebin(E.x)], 1u);
                 atomicAdd(&hsub[M::ebin(E.y)], 1u);
             };
@@ -1140,8 +1173,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const T E = v2 * half_m_over_e;
                 q[0].x += x; q[1].x += y; q[2].x += z;
                 q[3].x += x * x; q[4].x += y * y; q[5].x += z * z;
-                q[6].x += v;
-                q[7].x += E >= e_ion ? v : T(0);
+                if (!xs_on) {
+                    q[6].x += v;
+                    q[7].x += E >= e_ion ? v : T(0);
+                } else {
+                    q[6].x += xs_el<T>(a.xs, E, sg0) * v;
+                    q[7].x += xs_ion<T>(a.xs, E, si0, e_ion) * v;
+                }
                 atomicAdd(&hsub[M::ebin(E)], 1u);
             };
             if (do_neut && s_misc[2] > 0u) {
@@ -1249,8 +1287,8 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 m[1] = a.weight * N;
                 m[2] = s_tot[0]; m[3] = s_tot[1]; m[4] = s_tot[2];
                 m[5] = s_tot[3]; m[6] = s_tot[4]; m[7] = s_tot[5];
-                m[8] = a.sigma_el * s_tot[6];
-                m[9] = a.sigma_ion * s_tot[7];
+                m[8] = a.xs.on ? s_tot[6] : a.sigma_el * s_tot[6];
+                m[9] = a.xs.on ? s_tot[7] : a.sigma_ion * s_tot[7];
             }
         }
 

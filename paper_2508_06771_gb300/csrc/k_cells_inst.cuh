@@ -67,21 +67,28 @@ struct CellKernel {
 };
 
 // Launch wrapper of the home-order kernel of the bijection pairing mode
-// (one CTA of NT threads per cell of up to CAPL particles).
+// (one CTA of NT threads per cell of up to CAPL particles).  Two compiled
+// forms: constant cross sections, and tabulated ones (chosen per launch).
 template <class T, int NT, int CAPL>
 struct HomeKernel {
     static size_t smem() { return home_dyn_smem<T>((uint32_t)CAPL); }
     static cudaError_t prepare()
     {
-        static cudaError_t once = cudaFuncSetAttribute(k_home<T, NT, CAPL>,
+        static cudaError_t once = cudaFuncSetAttribute(k_home<T, NT, CAPL, false>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
-        return once;
+        static cudaError_t once_xs = cudaFuncSetAttribute(k_home<T, NT, CAPL, true>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        return once != cudaSuccess ? once : once_xs;
     }
     static cudaError_t occupancy(int* ctas)
     {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_home<T, NT, CAPL>, NT, smem());
+        int a = 0, b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_home<T, NT, CAPL, false>, NT, smem());
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_home<T, NT, CAPL, true>, NT, smem());
+        *ctas = a < b ? a : b;
+        return e;
     }
     static cudaError_t occupancy_grid(int* ctas)
     {
@@ -101,7 +108,10 @@ struct HomeKernel {
             if (e != cudaSuccess) return e;
             if (grid_ctas <= 0) grid_ctas = 1;
         }
-        k_home<T, NT, CAPL><<<grid_ctas, NT, smem(), st>>>(a);
+        if (a.xs.on)
+            k_home<T, NT, CAPL, true><<<grid_ctas, NT, smem(), st>>>(a);
+        else
+            k_home<T, NT, CAPL, false><<<grid_ctas, NT, smem(), st>>>(a);
         return cudaGetLastError();
     }
     static CellKernelEntry entry()

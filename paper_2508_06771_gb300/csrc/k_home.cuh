@@ -108,7 +108,7 @@ template <> struct Vec16<double> {
     }
 };
 
-template <class T, int NT, int CAPL>
+template <class T, int NT, int CAPL, bool XS>
 __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
 {
     using VW = Vec16<T>;
@@ -430,6 +430,8 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
         uint32_t* hsub = s_hist + ((tid >> 5) & 3u) * NBIN;
         const T half_m_over_e = a.c_half_m_over_e;
         const T e_ion = a.c_e_ion;
+        constexpr bool xs_on = XS;                 // tables: the rate sums take sigma(E) |v|
+        const T sg0 = a.c_sig_el, si0 = a.c_sig_ion;
         // one particle's contribution, into the first lane, with sign sg (+1 add, -1 remove)
         auto accum = [&](T x, T y, T z, T sg) {
             const T v2 = x * x + y * y + z * z;
@@ -437,8 +439,13 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             const T E = v2 * half_m_over_e;
             mq[0].x += sg * x; mq[1].x += sg * y; mq[2].x += sg * z;
             mq[3].x += sg * (x * x); mq[4].x += sg * (y * y); mq[5].x += sg * (z * z);
-            mq[6].x += sg * v;
-            mq[7].x += E >= e_ion ? sg * v : T(0);
+            if (!xs_on) {
+                mq[6].x += sg * v;
+                mq[7].x += E >= e_ion ? sg * v : T(0);
+            } else {
+                mq[6].x += sg * (xs_el<T>(a.xs, E, sg0) * v);
+                mq[7].x += sg * (xs_ion<T>(a.xs, E, si0, e_ion) * v);
+            }
             atomicAdd(&hsub[Math<T>::ebin(E)], sg > T(0) ? 1u : 0xFFFFFFFFu);
         };
         T vmax2 = T(0);
@@ -468,8 +475,14 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                     const V2 E = P::mul(v2, P::make(half_m_over_e, half_m_over_e));
                     P::acc(mq[0], X); P::acc(mq[1], Y); P::acc(mq[2], Z);
                     P::acc_sq(mq[3], X); P::acc_sq(mq[4], Y); P::acc_sq(mq[5], Z);
-                    P::acc(mq[6], V);
-                    P::acc(mq[7], P::make(E.x >= e_ion ? V.x : T(0), E.y >= e_ion ? V.y : T(0)));
+                    if (!xs_on) {
+                        P::acc(mq[6], V);
+                        P::acc(mq[7], P::make(E.x >= e_ion ? V.x : T(0), E.y >= e_ion ? V.y : T(0)));
+                    } else {
+                        P::acc(mq[6], P::make(xs_el<T>(a.xs, E.x, sg0) * V.x, xs_el<T>(a.xs, E.y, sg0) * V.y));
+                        P::acc(mq[7], P::make(xs_ion<T>(a.xs, E.x, si0, e_ion) * V.x,
+                                              xs_ion<T>(a.xs, E.y, si0, e_ion) * V.y));
+                    }
                     atomicAdd(&hsub[Math<T>::ebin(E.x)], 1u);
                     atomicAdd(&hsub[Math<T>::ebin(E.y)], 1u);
                 } else {
@@ -510,8 +523,8 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                 const T v2 = x * x + y * y + z * z;
                 const T v = Math<T>::sqrt(v2);
                 const T E = v2 * half_m_over_e;
-                const T nu_el = nsel * v;
-                const T nu_ion = E >= e_ion ? nsion * v : T(0);
+                const T nu_el = xs_on ? a.c_nn * xs_el<T>(a.xs, E, sg0) * v : nsel * v;
+                const T nu_ion = xs_on ? a.c_nn * xs_ion<T>(a.xs, E, si0, e_ion) * v : E >= e_ion ? nsion * v : T(0);
                 const T rr = unif<T>(rw.z) * numax;
                 if (rr < nu_el) {                              // C1: elastic, cold heavy target
                     const uint4 sc = draw(a.keys, l, step, TAG_SCATTER);
@@ -589,8 +602,8 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             m[1] = a.weight * N;
             m[2] = s_tot[0]; m[3] = s_tot[1]; m[4] = s_tot[2];
             m[5] = s_tot[3]; m[6] = s_tot[4]; m[7] = s_tot[5];
-            m[8] = a.sigma_el * s_tot[6];
-            m[9] = a.sigma_ion * s_tot[7];
+            m[8] = XS ? s_tot[6] : a.sigma_el * s_tot[6];
+            m[9] = XS ? s_tot[7] : a.sigma_ion * s_tot[7];
         }
         pc.mark(9);
 

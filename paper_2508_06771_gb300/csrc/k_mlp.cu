@@ -390,12 +390,13 @@ template <class T>
 __global__ void k_subsample(const T* __restrict__ vx, const T* __restrict__ vy, const T* __restrict__ vz,
                             const int32_t* __restrict__ cell, const uint32_t* __restrict__ counts,
                             unsigned long long n, uint32_t per_cell, uint32_t salt, uint64_t seed,
-                            double half_m_over_e, double sigma_el, double sigma_ion, double e_ion,
+                            double half_m_over_e, double sigma_el, double sigma_ion, double e_ion, XsArgs xs,
                             float* __restrict__ sub, uint32_t* __restrict__ subh)
 {
     for (unsigned long long l = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; l < n;
          l += (unsigned long long)gridDim.x * blockDim.x) {
         const int32_t c = cell[l];
+        if (c < 0) continue;                              // removed (wall, recombination)
         const uint32_t N = counts[c];
         if (N == 0) continue;
         const uint4 r = draw((uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)l, salt, 9u);
@@ -405,8 +406,8 @@ __global__ void k_subsample(const T* __restrict__ vx, const T* __restrict__ vy, 
         float* s = sub + (size_t)c * NMOM;
         atomicAdd(&s[0], 1.f);
         atomicAdd(&s[5], (float)v2);
-        atomicAdd(&s[8], (float)(sigma_el * v));
-        atomicAdd(&s[9], (float)(E >= e_ion ? sigma_ion * v : 0.0));
+        atomicAdd(&s[8], (float)(xs_el<double>(xs, E, sigma_el) * v));
+        atomicAdd(&s[9], (float)(xs_ion<double>(xs, E, sigma_ion, e_ion) * v));
         int b = 0;
         if (E > 0.0) {
             const double t = (log10(E) + 2.0) * 12.8;
@@ -640,6 +641,7 @@ extern "C" int ltpc_internal_particles_view(ltpc_ctx* ctx, const void** vx, cons
                                             const int32_t** cell, const uint32_t** counts, unsigned long long* n,
                                             int* precision, uint64_t* seed, double* sig_el, double* sig_ion,
                                             double* e_ion);
+extern "C" int ltpc_internal_xs_view(ltpc_ctx* ctx, XsArgs* xs);
 
 extern "C" int ltpc_mlp_features(ltpc_ctx* ctx, ltpc_mlp* p, float* d_X, float* d_T, int normalize)
 {
@@ -708,15 +710,18 @@ extern "C" int ltpc_mlp_subsample_features(ltpc_ctx* ctx, ltpc_mlp* p, int32_t p
     double se, si, ei;
     rc = ltpc_internal_particles_view(ctx, &vx, &vy, &vz, &cell, &counts, &n, &prec, &seed, &se, &si, &ei);
     if (rc) return rc;
+    XsArgs xs;
+    rc = ltpc_internal_xs_view(ctx, &xs);
+    if (rc) return rc;
     if (cudaMemsetAsync(p->sub, 0, (size_t)M * NMOM * 4, s) != cudaSuccess ||
         cudaMemsetAsync(p->subh, 0, (size_t)M * NBIN * 4, s) != cudaSuccess)
         return LTPC_ECUDA;
     if (prec == LTPC_F32)
         k_subsample<float><<<1024, 256, 0, s>>>((const float*)vx, (const float*)vy, (const float*)vz, cell, counts, n,
-                                                (uint32_t)per_cell, salt, seed, hme, se, si, ei, p->sub, p->subh);
+                                                (uint32_t)per_cell, salt, seed, hme, se, si, ei, xs, p->sub, p->subh);
     else
         k_subsample<double><<<1024, 256, 0, s>>>((const double*)vx, (const double*)vy, (const double*)vz, cell, counts,
-                                                 n, (uint32_t)per_cell, salt, seed, hme, se, si, ei, p->sub, p->subh);
+                                                 n, (uint32_t)per_cell, salt, seed, hme, se, si, ei, xs, p->sub, p->subh);
     k_sub_to_moments<<<(M + 255) / 256, 256, 0, s>>>(M, p->sub, p->subm);
     // the distribution features and the direct rate estimate come from the sample only; the
     // density feature is the cell's density (known exactly from its count)

@@ -31,7 +31,7 @@ struct Layout {
     size_t vx, vy, vz, cell, x;
     // work offsets
     size_t perm, counts, cell_start, cs_prev, cursor, ion_count, ion_off, stage_l, stage_vx, stage_vy,
-        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, accel, rec_count, lists, ds;
+        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, accel, rec_count, xs, lists, ds;
 };
 
 bool compute_layout(const ltpc_config* c, Layout* L)
@@ -71,6 +71,7 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->aslot = take(cap * 4);
     L->accel = take(M * 8);
     L->rec_count = take(M * 4);
+    L->xs = take((size_t)2 * XS_MAX_PIECES * 4 * (8 + 4));   // two tables, binary64 then binary32
     L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
     L->work = o;
@@ -108,6 +109,10 @@ struct ltpc_ctx {
     int32_t wall = LTPC_WALL_PERIODIC;
     // recombination C5 (ltpc_set_recombination)
     double k_rec = 0.0, de_rec = 0.0;
+    // tabulated cross sections and selection (ltpc_set_cross_sections)
+    XsArgs xs{};
+    bool xs_tables = false;
+    double sigma_max = 0.0;
     char cuda_err[256] = {0};
 
     template <class P> P* w(size_t off) const { return reinterpret_cast<P*>(wk + off); }
@@ -195,7 +200,11 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.c_two_e_over_m = (T)(2.0 * ctx->cfg.charge / ctx->cfg.mass);
     a.c_nsig_el = (T)(ctx->cfg.n_neutral * ctx->cfg.sigma_el);
     a.c_nsig_ion = (T)(ctx->cfg.n_neutral * ctx->cfg.sigma_ion);
-    a.c_nsig_tot = (T)(ctx->cfg.n_neutral * (ctx->cfg.sigma_el + ctx->cfg.sigma_ion));
+    a.c_nsig_tot = (T)(ctx->cfg.n_neutral * (ctx->xs_tables ? ctx->sigma_max : ctx->cfg.sigma_el + ctx->cfg.sigma_ion));
+    a.c_nn = (T)ctx->cfg.n_neutral;
+    a.c_sig_el = (T)ctx->cfg.sigma_el;
+    a.c_sig_ion = (T)ctx->cfg.sigma_ion;
+    a.xs = ctx->xs;
     a.c_e_ion = (T)ctx->cfg.e_ion;
     a.c_mratio2 = (T)a.mratio2;
     a.cell = ctx->s<int32_t>(L.cell);
@@ -558,6 +567,90 @@ int ltpc_set_recombination(ltpc_ctx* ctx, double k_rec, double de_rec)
     return LTPC_OK;
 }
 
+namespace {
+
+// Host value of one table: the same steps as the device's binary64 evaluator.
+double xs_host(const ltpc_xsec& t, double E)
+{
+    if (!(E > 0.0)) return t.zero_below ? 0.0 : t.coef[0];
+    const double u = (std::log(E) - t.lnE0) / t.h;
+    if (u < 0.0) return t.zero_below ? 0.0 : t.coef[0];
+    const double fi = std::floor(u);
+    int32_t i = (int32_t)fi;
+    double x;
+    if (i >= t.pieces) { i = t.pieces - 1; x = 1.0; }
+    else x = u - fi;
+    const double* c = t.coef + 4 * (size_t)i;
+    return c[0] + x * (c[1] + x * (c[2] + x * c[3]));
+}
+
+bool xs_valid(const ltpc_xsec* t)
+{
+    if (!t) return true;
+    if (t->pieces < 1 || t->pieces > XS_MAX_PIECES || (t->zero_below != 0 && t->zero_below != 1) || !t->coef)
+        return false;
+    if (!std::isfinite(t->lnE0) || !(t->h > 0.0) || !std::isfinite(t->h)) return false;
+    for (int i = 0; i < 4 * t->pieces; ++i)
+        if (!std::isfinite(t->coef[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+int ltpc_set_cross_sections(ltpc_ctx* ctx, const ltpc_xsec* el, const ltpc_xsec* ion, double sigma_max,
+                            int32_t selection)
+{
+    if (!ctx || !xs_valid(el) || !xs_valid(ion)) return LTPC_EINVAL;
+    if (selection != LTPC_SELECT_NULL && selection != LTPC_SELECT_PER_PARTICLE) return LTPC_EINVAL;
+    if (selection == LTPC_SELECT_PER_PARTICLE && ctx->cfg.pairing_mode != LTPC_PAIR_KEY) return LTPC_EINVAL;
+    const bool tables = el || ion;
+    if (tables && (!(sigma_max > 0.0) || !std::isfinite(sigma_max))) return LTPC_EINVAL;
+    // sample both tables (32 points per piece of each, and its knots): no negative
+    // value, no sum above sigma_max
+    const ltpc_xsec* tabs[2] = {el, ion};
+    for (const ltpc_xsec* t : tabs) {
+        if (!t) continue;
+        for (int i = 0; i <= 32 * t->pieces; ++i) {
+            const double E = std::exp(t->lnE0 + t->h * (double)i / 32.0);
+            const double se = el ? xs_host(*el, E) : ctx->cfg.sigma_el;
+            const double si = ion ? xs_host(*ion, E) : (E >= ctx->cfg.e_ion ? ctx->cfg.sigma_ion : 0.0);
+            if (!(se >= 0.0) || !(si >= 0.0) || se + si > sigma_max) return LTPC_EINVAL;
+        }
+    }
+    XsArgs x{};
+    x.on = tables || selection == LTPC_SELECT_PER_PARTICLE;
+    x.per_particle = selection == LTPC_SELECT_PER_PARTICLE;
+    double* dd = ctx->w<double>(ctx->L.xs);
+    float* df = reinterpret_cast<float*>(dd + 2 * XS_MAX_PIECES * 4);
+    std::vector<double> hd(2 * XS_MAX_PIECES * 4, 0.0);
+    std::vector<float> hf(2 * XS_MAX_PIECES * 4, 0.0f);
+    for (int k = 0; k < 2; ++k) {
+        XsTable& T = k == 0 ? x.el : x.ion;
+        const ltpc_xsec* t = tabs[k];
+        T.cd = dd + k * XS_MAX_PIECES * 4;
+        T.cf = df + k * XS_MAX_PIECES * 4;
+        if (!t) continue;
+        T.pieces = t->pieces;
+        T.zero_below = t->zero_below;
+        T.lnE0 = t->lnE0;
+        T.h = t->h;
+        T.lnE0f = (float)t->lnE0;
+        T.inv_hf = (float)(1.0 / t->h);
+        for (int i = 0; i < 4 * t->pieces; ++i) {
+            hd[k * XS_MAX_PIECES * 4 + i] = t->coef[i];
+            hf[k * XS_MAX_PIECES * 4 + i] = (float)t->coef[i];
+        }
+    }
+    CK(cudaMemcpyAsync(dd, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(df, hf.data(), hf.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->xs = x;
+    ctx->xs_tables = tables;
+    ctx->sigma_max = tables ? sigma_max : 0.0;
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    return LTPC_OK;
+}
+
 int ltpc_push(ltpc_ctx* ctx, double dt, int64_t step)
 {
     if (!ctx || !ctx->field) return LTPC_EINVAL;
@@ -801,6 +894,13 @@ int ltpc_internal_particles_view(ltpc_ctx* ctx, const void** vx, const void** vy
     *precision = ctx->cfg.precision;
     *seed = ctx->cfg.seed;
     *sig_el = ctx->cfg.sigma_el; *sig_ion = ctx->cfg.sigma_ion; *e_ion = ctx->cfg.e_ion;
+    return LTPC_OK;
+}
+
+int ltpc_internal_xs_view(ltpc_ctx* ctx, XsArgs* xs)
+{
+    if (!ctx || !xs) return LTPC_EINVAL;
+    *xs = ctx->xs;
     return LTPC_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "philox.cuh"
+#include "xsec.cuh"
 
 namespace ltpc {
 
@@ -119,6 +120,9 @@ struct CellArgs {
     T c_nsig_el, c_nsig_ion;     // n_n sigma_el, n_n sigma_ion
     T c_nsig_tot;                // n_n (sigma_el + sigma_ion), rounded once
     T c_e_ion, c_mratio2;
+    T c_nn;                      // n_n, for the tabulated cross sections
+    T c_sig_el, c_sig_ion;       // the constant cross sections (tables on, one of them absent)
+    XsArgs xs;                   // tabulated sigma_el(E), sigma_ion(E); per-particle selection
     int32_t* cell;               // cell id of every particle (C5 marks removed primaries with -1)
     uint32_t* rec_count;         // [M] primaries removed by this pass (C5)
     T c_de_rec;                  // energy released to the catalyte [eV]

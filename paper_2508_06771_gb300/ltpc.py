@@ -22,6 +22,8 @@ LOAD_SRC_DEVICE, LOAD_ASYNC = 1, 2   # flags of ltpc_load_particles
 LNL_CONST, LNL_NRL = 0, 1
 PAIR_KEY, PAIR_BIJECTION = 0, 1      # ltpc_config.pairing_mode
 WALL_PERIODIC, WALL_ABSORB = 0, 1    # ltpc_set_field
+SELECT_NULL, SELECT_PER_PARTICLE = 0, 1   # ltpc_set_cross_sections
+XS_MAX_PIECES = 256
 
 _lock = threading.Lock()
 _lib = None
@@ -50,6 +52,12 @@ class Config(C.Structure):
     ]
 
 
+class Xsec(C.Structure):
+    """One tabulated cross section (ltpc_xsec): piecewise cubic in ln E."""
+    _fields_ = [("pieces", C.c_int32), ("zero_below", C.c_int32), ("lnE0", C.c_double), ("h", C.c_double),
+                ("coef", C.c_void_p)]
+
+
 def load_library(path: str = LIB_PATH):
     """Load libltpc.so (raises if it has not been built)."""
     global _lib
@@ -69,6 +77,7 @@ def load_library(path: str = LIB_PATH):
             "ltpc_set_field": (C.c_int, [vp, C.c_double, vp, i32]),
             "ltpc_push": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_set_recombination": (C.c_int, [vp, C.c_double, C.c_double]),
+            "ltpc_set_cross_sections": (C.c_int, [vp, vp, vp, C.c_double, i32]),
             "ltpc_collide_coulomb": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_collide_neutral": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_step": (C.c_int, [vp, C.c_double, i64]),
@@ -187,6 +196,10 @@ class Collider:
                 has_position=wl.get("x") is not None, use_graph=use_graph,
                 dt_factor=np.asarray(wl["dt_cell"]) / dt, lnlambda=wl["lnlam_cell"], **kw)
         c.dt = dt
+        xs, sel = wl.get("xs"), int(wl.get("selection", SELECT_NULL))
+        if xs is not None or sel != SELECT_NULL:      # (elastic table, ionization table, sigma_max)
+            el, ion, smax = xs if xs is not None else (None, None, 0.0)
+            c.set_cross_sections(el, ion, smax, sel)
         return c
 
     # ------------------------------------------------------------------ plumbing
@@ -223,6 +236,21 @@ class Collider:
     def set_recombination(self, k_rec: float, de_rec: float):
         """Recombination C5: three-body rate k_rec [m^6/s], energy de_rec [eV] to the catalyte."""
         self._check(self.L.ltpc_set_recombination(self.ctx, float(k_rec), float(de_rec)), "set_recombination")
+
+    def set_cross_sections(self, el=None, ion=None, sigma_max: float = 0.0, selection: int = SELECT_NULL):
+        """Tabulated sigma_el(E) / sigma_ion(E) (dicts with pieces, zero_below, lnE0, h, coef [pieces, 4])
+        and the selection method (SELECT_NULL or SELECT_PER_PARTICLE)."""
+        keep, refs = [], []
+        for t in (el, ion):
+            if t is None:
+                refs.append(None)
+                continue
+            coef = np.ascontiguousarray(t["coef"], dtype=np.float64)
+            x = Xsec(int(t["pieces"]), int(t["zero_below"]), float(t["lnE0"]), float(t["h"]), coef.ctypes.data)
+            keep.append((coef, x))
+            refs.append(C.addressof(x))
+        self._check(self.L.ltpc_set_cross_sections(self.ctx, refs[0], refs[1], float(sigma_max), int(selection)),
+                    "set_cross_sections")
 
     def push(self, dt, step):
         self._check(self.L.ltpc_push(self.ctx, float(dt), int(step)), "push")
