@@ -31,6 +31,12 @@
  *                       uniformity of positions, partners and the left-out
  *                       particle; rate of neighbouring-rank pairs; candidate
  *                       count mean P_null N and uniform selection
+ *   orc_xs_eval         within 2 % of the smooth cross sections it tabulates,
+ *                       exact at the knots, zero below the threshold
+ *   per-particle selection (orc_neutral, selection 1)
+ *                       binomial counts against sum pi_c; same mean number of
+ *                       real collisions as the null-collision method to first
+ *                       order in dt; rate sums against a quadrature
  */
 #include <math.h>
 #include <stdint.h>

@@ -288,15 +288,24 @@ __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, 
     constexpr int G = 32 / NQ;                       // lanes per quantity
     constexpr int PER = (NW + G - 1) / G;            // warp partials per lane
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    // reduce-scatter butterfly: at offset o (16, 8, ...) a lane keeps one half of its
+    // remaining quantities (the upper half if bit o of its lane is set) and adds the
+    // partner's copy of that half, so after log2(NQ) levels lane l holds quantity
+    // l / G summed over its group of G lanes; the group is then closed by xor
+    // shuffles: NQ - 1 + log2(G) shuffles instead of 5 NQ
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) {
+    for (int h = NQ / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & (unsigned)o) != 0u;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xFFFFFFFFu, v[k], o);
+        for (int k = 0; k < h; ++k) {
+            const A send = up ? v[k] : v[k + h];
+            const A keep = up ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
+        }
     }
-    if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) s_red[warp * NQ + k] = v[k];
-    }
+    for (int o = G / 2; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], o);
+    if (lane % (unsigned)G == 0u) s_red[warp * NQ + lane / (unsigned)G] = v[0];
     __syncthreads();
     if (warp == 0) {
         const unsigned k = lane % NQ, g = lane / NQ;

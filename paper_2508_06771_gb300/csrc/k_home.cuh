@@ -413,7 +413,18 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                 }
             }
         }
-        if (tid == TK) cp_async_wait_all();                // the next cell's words, for the tables below
+        if (tid == TK) {
+            cp_async_wait_all();                           // the next cell's words, for the tables below
+            // the next cell's run into L2 now, a whole cell's work before its bulk loads
+            const uint4 nx = s_item[par ^ 1u];             // this thread's own copy, waited in step 3
+            if (nx.w != 0u && nx.y != 0u) {
+                const uint32_t nrs = s_run[par ^ 1u][0], nrl = min(s_run[par ^ 1u][1], nx.y);
+                if (nrl) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) prefetch_l2(gv[c] + nrs, (size_t)nrl * sizeof(T));
+                }
+            }
+        }
         __syncthreads();
         pc.mark(7);
         fill_round_tables(par ^ 1u);                       // the next cell's round functions
@@ -608,8 +619,7 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
         pc.mark(9);
 
         // ---- 8. write-back: the run interior as three bulk stores (their reads of the slots are
-        // waited at the next cell's start), the rest with plain stores; the next cell's run
-        // into L2 meanwhile
+        // waited at the next cell's start), the rest with plain stores
         if (tid == DM && bytes) {
             fence_proxy_async();
 #pragma unroll
@@ -624,16 +634,6 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             const uint32_t l = id_of(k);
 #pragma unroll
             for (int c = 0; c < 3; ++c) gv[c][l] = sv0[c * PAD + k + o];
-        }
-        if (tid == TK) {
-            const uint4 nx = s_item[par ^ 1u];             // this thread's own copy, waited in step 3
-            if (nx.w != 0u && nx.y != 0u) {
-                const uint32_t nrs = s_run[par ^ 1u][0], nrl = min(s_run[par ^ 1u][1], nx.y);
-                if (nrl) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) prefetch_l2(gv[c] + nrs, (size_t)nrl * sizeof(T));
-                }
-            }
         }
         __syncthreads();
         pc.mark(10);
