@@ -114,6 +114,24 @@ BIJ_HD uint32_t bij_dec_tab(const BijParams& B, const TAB& tab, uint32_t y)
     return L * B.b + R;
 }
 
+// The forward rounds with the same tables (round i reads its input R below b for
+// even i, a for odd i, as the inverse does).  Same result as bij_enc.
+template <class TAB>
+BIJ_HD uint32_t bij_enc_tab(const BijParams& B, const TAB& tab, uint32_t x)
+{
+    uint32_t L = bij_umulhi(x, B.mb);
+    uint32_t R = x - L * B.b;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint32_t m = (i & 1) ? B.b : B.a;
+        uint32_t t = L + (uint32_t)tab(i, R);
+        t = t >= m ? t - m : t;
+        L = R;
+        R = t;
+    }
+    return L * B.b + R;
+}
+
 // pi(r) and its inverse on [0, n) (cycle walking ends: the cycle of r in
 // [0, a b) returns to r < n).
 BIJ_HD uint32_t bij_forward(const BijParams& B, uint32_t r)

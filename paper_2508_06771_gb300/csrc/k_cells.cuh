@@ -517,6 +517,10 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     // candidate words: by home index during the sort, by position afterwards;
     // 16 bytes past the sort view's bucket counters, so the sort never overlaps it
     uint16_t* sw = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(sl + CAPL) + 16);
+    // bijection mode: the cell's six round functions as byte tables, in the space of
+    // the candidate words, which only the key sort uses (2 B per position >= 1.5 KB)
+    uint8_t (*const s_rt)[256] = reinterpret_cast<uint8_t (*)[256]>(sw);
+    static_assert(CAPL * 2 >= 6 * 256, "round-function tables in the candidate-word space");
     // sort-phase view (aliases the pair-phase arrays); ekl holds {key, id} by
     // bucket position, so one 64-bit access moves an entry and one 64-bit
     // compare orders two entries by (key, id)
@@ -608,28 +612,63 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
 
         pc.mark(0);
         // ---- 1b. home slice: particle ids (coalesced), pairing keys, bucket counts
-        uint32_t hl[ITEMS], hp[ITEMS];
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {   // all id loads in flight before their first use
-            const uint32_t k = tid + (uint32_t)i * NT;
-            hl[i] = k < nh ? __ldcs(a.perm + s + hb + k) : 0u;
-        }
         // Bijection pairing (the cell's record says so; uniform over the cluster):
         // the cell's index list is in ascending id order (storage grouped by cell),
         // so home index hb + k is the particle's id rank and its pairing position
         // is pi(hb + k) -- no keys, no sort.
         const uint32_t* bw = reinterpret_cast<const uint32_t*>(a.cpar + (size_t)j * NCP + CP_BIJ);
         const uint32_t bij_ab = __ldg(bw + CPB_AB);
+        // clusters of 8 in the bijection mode gather by pairing position (step 2): no home ids
+        constexpr bool GATHER_BY_POS = C >= 8;
+        const bool home_ids = !GATHER_BY_POS || bij_ab == 0u;
+        uint32_t hl[ITEMS], hp[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {   // all id loads in flight before their first use
+            const uint32_t k = tid + (uint32_t)i * NT;
+            hl[i] = home_ids && k < nh ? __ldcs(a.perm + s + hb + k) : 0u;
+            hp[i] = 0u;
+        }
         uint32_t multi = 0u;           // items whose bucket holds several entries
-        if (bij_ab != 0u) {
+        auto rt = [&](int i, uint32_t v) -> uint32_t { return s_rt[i][v]; };
+        // the bijection's shape (its keys are in the tables), formed where it is used
+        auto bij_shape_of = [&]() {
             BijParams B;
             B.n = n; B.a = bij_ab & 0xFFFFu; B.b = bij_ab >> 16; B.mb = __ldg(bw + CPB_MB);
+            return B;
+        };
+        if (bij_ab != 0u) {
+            const BijParams B = bij_shape_of();
+            if constexpr (C > 1) {
+                // the six round functions as byte tables (round i reads its input below b
+                // for even i, a for odd i), for the position owners' inverse in step 2;
+                // the previous cell's readers passed several barriers
+                for (uint32_t e = tid; e < 6u * 256u; e += NT) {
+                    const uint32_t i = e >> 8, v = e & 255u;
+                    const uint32_t m = (i & 1u) ? B.b : B.a, lim = (i & 1u) ? B.a : B.b;
+                    if (v < lim) s_rt[i][v] = (uint8_t)bij_round(v, __ldg(bw + CPB_KEY + i), m);
+                }
+                __syncthreads();
+                if constexpr (!GATHER_BY_POS) {      // the home CTA places its particles
 #pragma unroll
-            for (int q = 0; q < 6; ++q) B.key[q] = __ldg(bw + CPB_KEY + q);
+                    for (int i = 0; i < ITEMS; ++i) {
+                        const uint32_t k = tid + (uint32_t)i * NT;
+                        uint32_t y = 0u;
+                        if (k < nh) {
+                            y = bij_enc_tab(B, rt, hb + k);
+                            while (y >= n) y = bij_enc_tab(B, rt, y);
+                        }
+                        hp[i] = y;
+                    }
+                }
+            } else {                   // (single CTAs: the rounds computed, no tables)
+                BijParams K = B;
 #pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const uint32_t k = tid + (uint32_t)i * NT;
-                hp[i] = k < nh ? bij_forward(B, hb + k) : 0u;
+                for (int q = 0; q < 6; ++q) K.key[q] = __ldg(bw + CPB_KEY + q);
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    const uint32_t k = tid + (uint32_t)i * NT;
+                    hp[i] = k < nh ? bij_forward(K, hb + k) : 0u;
+                }
             }
             if (r == 0 && tid == 0) {   // the next work item, completed by the wait before phase 3
                 if (wnext < list_n) cp_async<16>(&s_item[par ^ 1u], a.list + wnext);
@@ -835,8 +874,33 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     cp_async<sizeof(T)>(svy + pos, a.vy + l);
                     cp_async<sizeof(T)>(svz + pos, a.vz + l);
                     sl[pos] = l;
-                    sw[pos] = (uint16_t)(hp[i] >> 16);
+                    if (bij_ab == 0u) sw[pos] = (uint16_t)(hp[i] >> 16);
                     if (a.order_out) a.order_out[s + pos] = l;
+                }
+            }
+            cp_async_wait_all();
+        } else if (GATHER_BY_POS && bij_ab != 0u) {
+            // Bijection mode, clusters of 8: each CTA gathers the particles of its own pairing positions
+            // (the inverse bijection gives the id rank, the cell's run or id list the id)
+            // straight from global memory with asynchronous copies, all in flight at once:
+            // in clusters of eight, random reads through L2 sustain a higher rate than
+            // random stores into the other CTAs' shared memory.  Same pair slots as S1.
+            const BijParams B = bij_shape_of();
+            const uint32_t rs = __ldg(a.run_start + j), rl = min(__ldg(a.run_len + j), n);
+            for (uint32_t p = tid; 2u * p < nloc; p += NT) {
+#pragma unroll
+                for (uint32_t u = 0; u < 2u; ++u) {
+                    const uint32_t q = 2u * p + u;
+                    if (q < nloc) {
+                        uint32_t x = bij_dec_tab(B, rt, pb + q);
+                        while (x >= n) x = bij_dec_tab(B, rt, x);
+                        const uint32_t l = x < rl ? rs + x : __ldg(a.perm + s + x);
+                        cp_async<sizeof(T)>(svx + q, a.vx + l);
+                        cp_async<sizeof(T)>(svy + q, a.vy + l);
+                        cp_async<sizeof(T)>(svz + q, a.vz + l);
+                        sl[q] = l;
+                        if (a.order_out) a.order_out[s + pb + q] = l;
+                    }
                 }
             }
             cp_async_wait_all();
@@ -853,9 +917,30 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     *Cl<C>::at(svx + lp, o) = x;
                     *Cl<C>::at(svy + lp, o) = y;
                     *Cl<C>::at(svz + lp, o) = z;
-                    *Cl<C>::at(sl + lp, o) = l;
-                    *Cl<C>::at(sw + lp, o) = (uint16_t)(hp[i] >> 16);
+                    if (bij_ab == 0u) {
+                        *Cl<C>::at(sl + lp, o) = l;
+                        *Cl<C>::at(sw + lp, o) = (uint16_t)(hp[i] >> 16);
+                    }
                     if (a.order_out) a.order_out[s + pos] = l;
+                }
+            }
+            // Bijection mode: the position owner finds each position's id itself (the
+            // inverse bijection gives the id rank, the cell's run or id list the id)
+            // instead of receiving it: remote stores are the slowest shared-memory
+            // access on this GPU.  Same pair slots as step S1 below, so no barrier between.
+            if (bij_ab != 0u) {
+                const BijParams B = bij_shape_of();
+                const uint32_t rs = __ldg(a.run_start + j), rl = min(__ldg(a.run_len + j), n);
+                for (uint32_t p = tid; 2u * p < nloc; p += NT) {
+#pragma unroll
+                    for (uint32_t u = 0; u < 2u; ++u) {
+                        const uint32_t q = 2u * p + u;
+                        if (q < nloc) {
+                            uint32_t x = bij_dec_tab(B, rt, pb + q);
+                            while (x >= n) x = bij_dec_tab(B, rt, x);
+                            sl[q] = x < rl ? rs + x : __ldg(a.perm + s + x);
+                        }
+                    }
                 }
             }
             if (tid == 0) cp_async_wait_all();

@@ -3,7 +3,9 @@
 //     x < 256 b (all shapes of cells up to 65536 particles);
 //   * for each request "n k0 k1 k2 k3 k4 k5" on stdin, prints a, b, then pi(r)
 //     for r = 0..n-1 and the inverse at every position, for comparison with the
-//     oracle's table by the Python test.
+//     oracle's table by the Python test;
+//   * the table-driven rounds (bij_enc_tab, bij_dec_tab, as the kernels run them)
+//     give the same pi and inverse.
 #include <cstdio>
 #include "../paper_2508_06771_gb300/csrc/bijection.cuh"
 using namespace ltpc;
@@ -20,6 +22,22 @@ int main() {
         B.n = n;
         bij_shape(n, &B.a, &B.b, &B.mb);
         for (int i = 0; i < 6; ++i) B.key[i] = k[i];
+        static unsigned char tab[6][256];
+        for (int i = 0; i < 6; ++i) {
+            const uint32_t m = (i & 1) ? B.b : B.a, lim = (i & 1) ? B.a : B.b;
+            for (uint32_t r = 0; r < lim; ++r) tab[i][r] = (unsigned char)bij_round(r, B.key[i], m);
+        }
+        auto rt = [&](int i, uint32_t r) -> uint32_t { return tab[i][r]; };
+        for (uint32_t r = 0; r < n; ++r) {
+            uint32_t y = bij_enc_tab(B, rt, r);
+            while (y >= n) y = bij_enc_tab(B, rt, y);
+            uint32_t x = bij_dec_tab(B, rt, r);
+            while (x >= n) x = bij_dec_tab(B, rt, x);
+            if (y != bij_forward(B, r) || x != bij_inverse(B, r)) {
+                std::printf("FAIL tables n=%u r=%u\n", n, r);
+                return 1;
+            }
+        }
         std::printf("%u %u\n", B.a, B.b);
         for (uint32_t r = 0; r < n; ++r) std::printf("%u ", bij_forward(B, r));
         std::printf("\n");
