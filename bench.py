@@ -133,8 +133,14 @@ def make_workload(name, seed, rank=0, cells=None):
         wl = W.relax_64x1000(seed=seed)
         desc = "relax_64x1000: 64 cells x 1000 electrons, FP64, anisotropic Maxwellian, Coulomb only"
     elif name == "loguniform_256x256":
-        wl = W.loguniform_256x256(seed=seed, dtype=np.float32)
-        desc = f"loguniform_256x256: 256x256 cells, log-uniform 16..65536 per cell (N0={wl['vx'].size:,}), FP32, NRL lnL, Coulomb"
+        if cells:       # profiling cases: the first `cells` cells (whole 64-cell blocks) only
+            wl = W.loguniform_256x256(seed=seed, dtype=np.float32, blocks=list(range((cells + W.BLOCK - 1) // W.BLOCK)))
+            wl["capacity"] = max(1, wl["vx"].size)
+            sub = f" (cells 0..{min(cells, wl['M']) - 1} populated only)"
+        else:
+            wl = W.loguniform_256x256(seed=seed, dtype=np.float32)
+            sub = ""
+        desc = f"loguniform_256x256: 256x256 cells, log-uniform 16..65536 per cell{sub} (N0={wl['vx'].size:,}), FP32, NRL lnL, Coulomb"
     elif name == "instances_64":
         wl = W.instances_64(seed=seed, dtype=np.float32)
         desc = f"instances_64: 64 instances, {wl['M']} cells, N0={wl['vx'].size:,}, FP32, per-instance dt, Coulomb"
@@ -815,7 +821,8 @@ def main():
     ap.add_argument("--no-push-leg", action="store_true", help="skip the push (re-grouping every step) leg")
     ap.add_argument("--pairing", default="bijection", choices=["key", "bijection"],
                     help="in-cell pairing: key sort, or the keyed bijection for cells above 4096")
-    ap.add_argument("--cells", type=int, default=None, help="tail_4096x10000 only: number of cells (profiling cases)")
+    ap.add_argument("--cells", type=int, default=None,
+                    help="tail_4096x10000 and loguniform_256x256 only: number of cells (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
