@@ -495,6 +495,10 @@ def run_ours(args, rank, world, local_rank):
         col.step(dt, k)
         net.infer(col, rates)
 
+    # storage compaction inside the timed region when the workload appends particles
+    appends = bool(wl.get("neutral", False) and wl.get("n_neutral", 0.0) > 0)
+    compact_every = args.compact_every if appends else 0
+
     step = 0
     # ---- accuracy probe: the first step's moments of sampled cells (compared with the oracle
     # in the CPU-baseline leg, the only place the benchmark runs it)
@@ -526,6 +530,8 @@ def run_ours(args, rank, world, local_rank):
         e0.record(stream)
         for k in range(args.steps):
             full_step(step + k)
+            if compact_every and (k + 1) % compact_every == 0:
+                col.compact()                    # appended particles back into their cells' runs
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -537,6 +543,10 @@ def run_ours(args, rank, world, local_rank):
     ms_max, upd_all = reduce_over_ranks(ms, updates, world, "cuda")
     value = upd_all / (ms_max / 1e3)
     launches_per_step = 3 + len(classes) + 3      # scatter, cells per class, regroup, append; surrogate x3
+    # a compaction: scatter, cursors, gather; the load's state, histogram, finite check, two run
+    # kernels, regroup; the moments pass (scatter, cells per class, regroup, append)
+    launches_per_compaction = 3 + 6 + 3 + len(classes) + 1   # and the step state before the next replay
+    n_compactions = args.steps // compact_every if compact_every else 0
     # in-loop check: surrogate rates of the last step against the exact particle reduction
     _, exact = net.features(col, normalize=False)
     pred = net.infer(col)
@@ -786,7 +796,8 @@ def run_ours(args, rank, world, local_rank):
                        "class_table_index": table, "autotuned": not args.no_autotune,
                        "pairing": ("keyed bijection of id ranks for cells > 4096 (candidates by pairing position), "
                                    "key sort below" if args.pairing == "bijection" else "key sort"),
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "compact_every": compact_every or None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": names[dom],
                          "kernel_ms": float(avg[dom]), "algorithmic_bytes": int(alg_bytes),
@@ -795,7 +806,7 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "cached_grouping": cached,
-            "gpu_launches": int(launches_per_step * args.steps),
+            "gpu_launches": int(launches_per_step * args.steps + launches_per_compaction * n_compactions),
             "clocks": clocks,
             "fp64_plain": fp64,
             "accuracy": accuracy,
@@ -823,6 +834,8 @@ def main():
                     help="in-cell pairing: key sort, or the keyed bijection for cells above 4096")
     ap.add_argument("--cells", type=int, default=None,
                     help="tail_4096x10000 and loguniform_256x256 only: number of cells (profiling cases)")
+    ap.add_argument("--compact-every", type=int, default=200,
+                    help="steps between storage compactions in the timed region (0: never; workloads with appends)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

@@ -166,6 +166,20 @@ int ltpc_load_particles(ltpc_ctx* ctx, int64_t n, const int32_t* cell, const voi
  * bijection mode relies on).  Synchronizing.  Errors: EINVAL. */
 int ltpc_set_field(ltpc_ctx* ctx, double dx, const double* accel, int32_t boundary);
 
+/* Storage compaction.  Rewrites the particles in the order of the current
+ * per-cell grouping: cells ascending, each cell's particles contiguous (for
+ * storage grouped by cell, the cell's loaded run and then its appended
+ * particles in their append order), removed particles (cell -1) dropped.
+ * Particle ids become the new storage indices, so the random streams that
+ * later steps draw change with them; the moments are recomputed by a
+ * collision-free pass, as after a load.  Between compactions the particles
+ * appended by ionization stay outside their cell's run, where every pass
+ * reaches them with scattered accesses; compacting every few hundred steps
+ * keeps the runs whole.  Reads the grouped count back (one synchronization of
+ * the stream), then proceeds asynchronously like a load with LTPC_LOAD_ASYNC.
+ * Errors: a pending sticky error, ECUDA. */
+int ltpc_compact(ltpc_ctx* ctx);
+
 /* Steps S2b/S2c alone (no collisions) with time step dt (cell j: dt *
  * dt_factor[j]) at step number `step`, then the grouping of the new cells and
  * their moments.  Needs ltpc_set_field.  Asynchronous.  Errors: EINVAL. */

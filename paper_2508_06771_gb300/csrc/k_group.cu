@@ -520,6 +520,40 @@ cudaError_t launch_runs(const int32_t* cell, int32_t M, const uint32_t* counts, 
     return cudaGetLastError();
 }
 
+// Storage compaction: dst[k] = src[perm[k]] for the k < n grouped particles (cells
+// ascending, each cell's particles in its grouping order).  Reads follow the id
+// list (runs of consecutive ids for cell-grouped storage), writes are coalesced.
+template <class T>
+static __global__ void __launch_bounds__(256) k_compact_gather(const uint32_t* __restrict__ perm, uint32_t n,
+                                                               const T* __restrict__ a0, const T* __restrict__ a1,
+                                                               const T* __restrict__ a2, const int32_t* __restrict__ c,
+                                                               T* __restrict__ b0, T* __restrict__ b1, T* __restrict__ b2,
+                                                               int32_t* __restrict__ d)
+{
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t l = perm[k];
+        b0[k] = a0[l];
+        if (b1) b1[k] = a1[l];
+        if (b2) b2[k] = a2[l];
+        if (d) d[k] = c[l];
+    }
+}
+
+template <class T>
+cudaError_t launch_compact_gather(const uint32_t* perm, uint32_t n, const T* a0, const T* a1, const T* a2,
+                                  const int32_t* c, T* b0, T* b1, T* b2, int32_t* d, int grid, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int g = (int)min((unsigned long long)grid, ((unsigned long long)n + 255ull) / 256ull);
+    k_compact_gather<T><<<g, 256, 0, s>>>(perm, n, a0, a1, a2, c, b0, b1, b2, d);
+    return cudaGetLastError();
+}
+template cudaError_t launch_compact_gather<float>(const uint32_t*, uint32_t, const float*, const float*, const float*,
+                                                  const int32_t*, float*, float*, float*, int32_t*, int, cudaStream_t);
+template cudaError_t launch_compact_gather<double>(const uint32_t*, uint32_t, const double*, const double*,
+                                                   const double*, const int32_t*, double*, double*, double*, int32_t*,
+                                                   int, cudaStream_t);
+
 cudaError_t launch_reset_cursors(int32_t M, const uint32_t* cell_start, const RegroupLists& runs, uint32_t* cursor,
                                  cudaStream_t s)
 {

@@ -810,6 +810,43 @@ int ltpc_pair_order(ltpc_ctx* ctx, int64_t step, uint32_t* d_order, uint32_t* d_
     return rc;
 }
 
+int ltpc_compact(ltpc_ctx* ctx)
+{
+    if (!ctx) return LTPC_EINVAL;
+    int rc = read_errors(ctx);
+    if (rc) return rc;
+    const Layout& L = ctx->L;
+    const int32_t M = ctx->cfg.n_cells;
+    cudaStream_t s = ctx->stream;
+    // the grouping of the current particles (CCS3 into perm), then the cursors back
+    CK(launch_scatter(ctx->s<int32_t>(L.cell), M, ctx->w<uint32_t>(L.cursor), ctx->w<uint32_t>(L.perm), ctx->ds,
+                      ctx->sms * 8, s, ctx->lists, ctx->w<uint32_t>(L.cell_start)));
+    CK(launch_reset_cursors(M, ctx->w<uint32_t>(L.cell_start), ctx->lists, ctx->w<uint32_t>(L.cursor), s));
+    uint32_t ng = 0;
+    CK(cudaMemcpyAsync(&ng, ctx->w<uint32_t>(L.cell_start) + M, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t* perm = ctx->w<uint32_t>(L.perm);
+    int32_t* dcell = reinterpret_cast<int32_t*>(ctx->w<uint32_t>(L.stage_l));
+    const int grid = ctx->sms * 8;
+    auto gather = [&](auto tag) -> int {
+        using T = decltype(tag);
+        T* b0 = ctx->w<T>(L.stage_vx);
+        T* b1 = ctx->w<T>(L.stage_vy);
+        T* b2 = ctx->w<T>(L.stage_vz);
+        if (ctx->cfg.has_position) {                      // positions first, in place through the stage
+            CK(launch_compact_gather<T>(perm, ng, ctx->s<T>(L.x), nullptr, nullptr, nullptr, b0, nullptr, nullptr,
+                                        nullptr, grid, s));
+            CK(cudaMemcpyAsync(ctx->st + L.x, b0, (size_t)ng * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        }
+        CK(launch_compact_gather<T>(perm, ng, ctx->s<T>(L.vx), ctx->s<T>(L.vy), ctx->s<T>(L.vz),
+                                    ctx->s<int32_t>(L.cell), b0, b1, b2, dcell, grid, s));
+        // the compacted particles loaded from the stage: counts, runs, grouping, moments
+        return ltpc_load_particles(ctx, (int64_t)ng, dcell, nullptr, b0, b1, b2,
+                                   LTPC_LOAD_SRC_DEVICE | LTPC_LOAD_ASYNC);
+    };
+    return ctx->cfg.precision == LTPC_F32 ? gather(float{}) : gather(double{});
+}
+
 int ltpc_grouping(ltpc_ctx* ctx, uint32_t* d_cell_start, uint32_t* d_perm, uint32_t* d_counts)
 {
     if (!ctx) return LTPC_EINVAL;

@@ -69,6 +69,9 @@ cudaError_t launch_scatter(const int32_t* cell, int32_t M, uint32_t* cursor, uin
                            const CellParamArgs* cp = nullptr);
 cudaError_t launch_runs(const int32_t* cell, int32_t M, const uint32_t* counts, const RegroupLists& runs, DevState* ds,
                         int grid, cudaStream_t s, int require_grouped);
+template <class T>
+cudaError_t launch_compact_gather(const uint32_t* perm, uint32_t n, const T* a0, const T* a1, const T* a2,
+                                  const int32_t* c, T* b0, T* b1, T* b2, int32_t* d, int grid, cudaStream_t s);
 cudaError_t launch_reset_cursors(int32_t M, const uint32_t* cell_start, const RegroupLists& runs, uint32_t* cursor,
                                  cudaStream_t s);
 cudaError_t launch_regroup(int32_t M, uint32_t* counts, uint32_t* cell_start, uint32_t* cs_prev, uint32_t* cursor,

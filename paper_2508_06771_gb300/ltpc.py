@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
             "ltpc_push": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_set_recombination": (C.c_int, [vp, C.c_double, C.c_double]),
             "ltpc_set_cross_sections": (C.c_int, [vp, vp, vp, C.c_double, i32]),
+            "ltpc_compact": (C.c_int, [vp]),
             "ltpc_collide_coulomb": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_collide_neutral": (C.c_int, [vp, C.c_double, i64]),
             "ltpc_step": (C.c_int, [vp, C.c_double, i64]),
@@ -251,6 +252,11 @@ class Collider:
             refs.append(C.addressof(x))
         self._check(self.L.ltpc_set_cross_sections(self.ctx, refs[0], refs[1], float(sigma_max), int(selection)),
                     "set_cross_sections")
+
+    def compact(self):
+        """Rewrite the storage grouped by cell (appended particles into their cell's run, removed
+        ones dropped); ids become the new storage indices."""
+        self._check(self.L.ltpc_compact(self.ctx), "compact")
 
     def push(self, dt, step):
         self._check(self.L.ltpc_push(self.ctx, float(dt), int(step)), "push")
