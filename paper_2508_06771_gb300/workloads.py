@@ -236,6 +236,9 @@ def subset_cells(wl: dict, cells) -> dict:
     out["capacity"] = max(int(keep.sum()) * 2, 1)
     if wl.get("x") is not None:
         out["x"] = wl["x"][keep]
+    for key in ("instance_of_cell", "counts"):            # other per-cell arrays
+        if wl.get(key) is not None:
+            out[key] = np.asarray(wl[key])[cells]
     return out
 
 

@@ -22,3 +22,14 @@ def test_subset_with_ids_equals_full_run(orc):
     sm, sh = orc.moments(sub, P)
     np.testing.assert_array_equal(sm, fm[cells])
     np.testing.assert_array_equal(sh, fh[cells])
+
+
+def test_subset_keeps_per_cell_arrays_aligned():
+    """A subset of an instance batch carries each kept cell's instance label and count."""
+    full = W.instances_64(seed=0, instances=[0, 1])
+    cells = np.array([0, 7, full["M"] - 1])
+    sub = W.subset_cells(full, cells)
+    assert np.array_equal(sub["instance_of_cell"], np.asarray(full["instance_of_cell"])[cells])
+    assert sub["instance_of_cell"].size == sub["M"] == cells.size
+    assert np.array_equal(np.bincount(sub["cell"], minlength=sub["M"]),
+                          np.bincount(full["cell"], minlength=full["M"])[cells])
