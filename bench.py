@@ -417,8 +417,15 @@ def relaxation_check(ltpc, steps=100):
                               method="DOP853", max_step=t[1] - t[0])
     rp, rq = sol.y
     dT = np.array(Tpar) - np.array(Tperp)
-    k = -np.polyfit(t, np.log(dT), 1)[0]
-    kr = -np.polyfit(t, np.log(rp - rq), 1)[0]
+    # exponential rates fitted over the leading steps where each difference is still above 5 % of
+    # the initial one (later the NRL curve reaches the noise floor, and the sample's difference
+    # the sampling noise of 64,000 particles)
+    def lead(d):
+        ok = d > 0.05 * d[0]
+        return np.arange(int(np.argmin(ok)) if not ok.all() else ok.size)
+    s1, s2 = lead(dT), lead(rp - rq)
+    k = -np.polyfit(t[s1], np.log(dT[s1]), 1)[0]
+    kr = -np.polyfit(t[s2], np.log((rp - rq)[s2]), 1)[0]
     Tm = (np.array(Tpar) + 2 * np.array(Tperp)) / 3
     return {"workload": "relax_64x1000, FP64, 100 Coulomb steps", "rate_ratio_to_nrl": float(k / kr),
             "expected_ratio_at_this_dt": "about 0.74 (deficit ~ dt^(1/3); the oracle's pin extrapolates to 1)",
