@@ -156,6 +156,55 @@ __device__ __forceinline__ void ta_delta(T ax, T ay, T az, T bx, T by, T bz, T A
     }
 }
 
+// Two independent pairs at once: pair 0 in the .x lanes, pair 1 in the .y lanes of
+// packed binary32 operations, the SFU functions per lane (the steps of ta_delta).
+__device__ __forceinline__ void ta_delta2(float2 ax, float2 ay, float2 az, float2 bx, float2 by, float2 bz, float A,
+                                          const uint4& w0, const uint4& w1, float2& dux, float2& duy, float2& duz)
+{
+    using M = Math<float>;
+    auto neg = [](float2 v) { return make_float2(-v.x, -v.y); };
+    auto mk = [](float a, float b) { return make_float2(a, b); };
+    const float2 ux = __fadd2_rn(ax, neg(bx)), uy = __fadd2_rn(ay, neg(by)), uz = __fadd2_rn(az, neg(bz));
+    const float2 up2 = __ffma2_rn(uy, uy, __fmul2_rn(ux, ux));
+    const float2 usq = __ffma2_rn(uz, uz, up2);
+    const float2 u = mk(M::sqrt(usq.x), M::sqrt(usq.y));
+    const float2 iu = mk(M::rcp(u.x), M::rcp(u.y));
+    const float2 var = __fmul2_rn(__fmul2_rn(__fmul2_rn(mk(A, A), iu), iu), iu);
+    float sth0, cth0, sph0, cph0, sth1, cth1, sph1, cph1;
+    M::sincos2pi(unif_angle<float>(w0.y), &sth0, &cth0);
+    M::sincos2pi(unif_angle<float>(w0.z), &sph0, &cph0);
+    M::sincos2pi(unif_angle<float>(w1.y), &sth1, &cth1);
+    M::sincos2pi(unif_angle<float>(w1.z), &sph1, &cph1);
+    const float2 lg = mk(M::ln(unif<float>(w0.x)), M::ln(unif<float>(w1.x)));
+    const float2 vv = __fmul2_rn(var, __fmul2_rn(mk(-2.f, -2.f), lg));
+    const float2 delta = __fmul2_rn(mk(M::sqrt(vv.x), M::sqrt(vv.y)), mk(cth0, cth1));
+    const bool s0 = fabsf(delta.x) <= 1.f, s1 = fabsf(delta.y) <= 1.f;
+    const float2 t = mk(s0 ? delta.x : M::rcp(delta.x), s1 ? delta.y : M::rcp(delta.y));
+    const float2 q = __ffma2_rn(t, t, mk(1.f, 1.f));
+    const float2 rr = mk(M::rcp(q.x), M::rcp(q.y));
+    const float2 t2rr = __fmul2_rn(__fmul2_rn(mk(2.f, 2.f), t), rr);      // sin(Theta)
+    const float2 big = __fmul2_rn(mk(2.f, 2.f), rr);
+    const float2 smallv = __fmul2_rn(t2rr, t);
+    const float2 omc = mk(s0 ? smallv.x : big.x, s1 ? smallv.y : big.y);    // 1 - cos(Theta)
+    const float2 uperp = mk(M::sqrt(up2.x), M::sqrt(up2.y));
+    const bool p0 = up2.x > 0.f, p1 = up2.y > 0.f;
+    const float2 ip = mk(p0 ? M::rcp(uperp.x) : 0.f, p1 ? M::rcp(uperp.y) : 0.f);
+    const float2 cph = mk(cph0, cph1), sph = mk(sph0, sph1);
+    const float2 ca = __fmul2_rn(__fmul2_rn(__fmul2_rn(uz, t2rr), cph), ip);
+    const float2 cb = __fmul2_rn(__fmul2_rn(__fmul2_rn(u, t2rr), sph), ip);
+    // general case
+    float2 gx = __ffma2_rn(neg(ux), omc, __ffma2_rn(neg(uy), cb, __fmul2_rn(ux, ca)));
+    float2 gy = __ffma2_rn(neg(uy), omc, __ffma2_rn(ux, cb, __fmul2_rn(uy, ca)));
+    float2 gz = __ffma2_rn(neg(uz), omc, __fmul2_rn(neg(__fmul2_rn(uperp, t2rr)), cph));
+    // u_perp = 0
+    const float2 us = __fmul2_rn(u, t2rr);
+    const float2 hx = __fmul2_rn(us, cph), hy = __fmul2_rn(us, sph), hz = __fmul2_rn(neg(uz), omc);
+    const bool z0 = usq.x == 0.f, z1 = usq.y == 0.f;
+    dux = mk(z0 ? 0.f : (p0 ? gx.x : hx.x), z1 ? 0.f : (p1 ? gx.y : hx.y));
+    duy = mk(z0 ? 0.f : (p0 ? gy.x : hy.x), z1 ? 0.f : (p1 ? gy.y : hy.y));
+    duz = mk(z0 ? 0.f : (p0 ? gz.x : hz.x), z1 ? 0.f : (p1 ? gz.y : hz.y));
+}
+
 // Isotropic unit vector from two uniforms: cos(theta) = 1 - 2 U_a, phi = 2 pi U_b.
 template <class T>
 __device__ __forceinline__ void iso_dir(uint32_t wa, uint32_t wb, T& dx, T& dy, T& dz)

@@ -355,10 +355,9 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             };
             const bool pre = do_corr && !pre_mom;
             const V2 H = P::make(T(0.5), T(-0.5));
-#pragma unroll
-            for (int i = 0; i < PS; ++i) {
+            auto slot = [&](int i) {
                 const uint32_t p = tid + (uint32_t)i * NT;
-                if (2u * p >= n) continue;
+                if (2u * p >= n) return;
                 const uint32_t ka = pk[i] & 0xFFFFu, kb = pk[i] >> 16;
                 if (2u * p + 1u < n) {
                     const uint32_t la = id_of(ka), lb = id_of(kb);
@@ -380,6 +379,39 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                     if (pre) psum(X1, Y1, Z1, bx0, by0, bz0, bs0);
                     if (do_corr) psum(X1, Y1, Z1, sx, sy, sz, ss);
                 }
+            };
+            // binary32: two pair slots of a thread at once, in the two lanes of packed
+            // operations (the slot pairs i, i+1 are both full pairs except near the end)
+            const V2 HP = P::make(T(0.5), T(0.5)), HN = P::make(T(-0.5), T(-0.5));
+#pragma unroll
+            for (int i = 0; i < PS; i += 2) {
+                if constexpr (sizeof(T) == 4) {
+                    const uint32_t p1 = tid + (uint32_t)(i + 1) * NT;
+                    if (i + 1 < PS && 2u * p1 + 1u < n) {       // two full pairs: packed lanes
+                        const uint32_t ka0 = pk[i] & 0xFFFFu, kb0 = pk[i] >> 16;
+                        const uint32_t ka1 = pk[i + 1] & 0xFFFFu, kb1 = pk[i + 1] >> 16;
+                        const uint32_t la0 = id_of(ka0), lb0 = id_of(kb0), la1 = id_of(ka1), lb1 = id_of(kb1);
+                        V2 AX = P::make(svx[ka0], svx[ka1]), AY = P::make(svy[ka0], svy[ka1]);
+                        V2 AZ = P::make(svz[ka0], svz[ka1]);
+                        V2 BX = P::make(svx[kb0], svx[kb1]), BY = P::make(svy[kb0], svy[kb1]);
+                        V2 BZ = P::make(svz[kb0], svz[kb1]);
+                        if (pre) { psum(AX, AY, AZ, bx0, by0, bz0, bs0); psum(BX, BY, BZ, bx0, by0, bz0, bs0); }
+                        const uint4 w0 = draw(a.keys, la0 < lb0 ? la0 : lb0, step, TAG_PAIR);
+                        const uint4 w1 = draw(a.keys, la1 < lb1 ? la1 : lb1, step, TAG_PAIR);
+                        V2 DX, DY, DZ;
+                        ta_delta2(AX, AY, AZ, BX, BY, BZ, A, w0, w1, DX, DY, DZ);
+                        AX = P::fma(HP, DX, AX); AY = P::fma(HP, DY, AY); AZ = P::fma(HP, DZ, AZ);
+                        BX = P::fma(HN, DX, BX); BY = P::fma(HN, DY, BY); BZ = P::fma(HN, DZ, BZ);
+                        svx[ka0] = AX.x; svy[ka0] = AY.x; svz[ka0] = AZ.x;
+                        svx[ka1] = AX.y; svy[ka1] = AY.y; svz[ka1] = AZ.y;
+                        svx[kb0] = BX.x; svy[kb0] = BY.x; svz[kb0] = BZ.x;
+                        svx[kb1] = BX.y; svy[kb1] = BY.y; svz[kb1] = BZ.y;
+                        if (do_corr) { psum(AX, AY, AZ, sx, sy, sz, ss); psum(BX, BY, BZ, sx, sy, sz, ss); }
+                        continue;
+                    }
+                }
+                slot(i);
+                if (i + 1 < PS) slot(i + 1);
             }
             if (do_corr) {
                 T acc[8] = {sx.x + sx.y, sy.x + sy.y, sz.x + sz.y, ss.x + ss.y,

@@ -379,6 +379,7 @@ static const ClassTable kTabF32Bij[] = {
     {6, {0, 5, 10, 8, 9, 4}},  // home order up to 12288, then clusters of 2 and 4 1024-thread CTAs, 8 x 512
     {5, {0, 5, 10, 3, 4}},     // home order up to 12288, then clusters of 8 (256/512 threads)
     {6, {0, 5, 6, 8, 9, 4}},   // the cluster kernel (one CTA) up to 12288 instead of the home order
+    {3, {5, 10, 4}},           // few classes: key sort up to 4096, home order up to 12288, clusters of 8
 };
 static const ClassTable kTabF64Bij[] = {
     {6, {0, 5, 8, 7, 3, 4}},   // home order up to 6144, then clusters of 2/8
