@@ -53,6 +53,17 @@ BIJ_HD uint32_t bij_mix(uint32_t t)
 
 BIJ_HD uint32_t bij_round(uint32_t r, uint32_t key, uint32_t m) { return bij_umulhi(bij_mix(r ^ key), m); }
 
+// t mod m for t < 2m, without a branch: t - m wraps to above t when t < m.
+BIJ_HD uint32_t bij_reduce(uint32_t t, uint32_t m)
+{
+    const uint32_t u = t - m;
+#if defined(__CUDA_ARCH__)
+    return min(t, u);
+#else
+    return u < t ? u : t;
+#endif
+}
+
 // a = ceil(sqrt(n)), b = ceil(n / a), mb = ceil(2^32 / b) (n >= 2).
 BIJ_HD void bij_shape(uint32_t n, uint32_t* a, uint32_t* b, uint32_t* mb)
 {
@@ -71,8 +82,7 @@ BIJ_HD uint32_t bij_enc(const BijParams& B, uint32_t x)
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const uint32_t m = (i & 1) ? B.b : B.a;
-        uint32_t t = L + bij_round(R, B.key[i], m);
-        t = t >= m ? t - m : t;
+        const uint32_t t = bij_reduce(L + bij_round(R, B.key[i], m), m);
         L = R;
         R = t;
     }
@@ -86,8 +96,7 @@ BIJ_HD uint32_t bij_dec(const BijParams& B, uint32_t y)
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
         const uint32_t m = (i & 1) ? B.b : B.a;
-        uint32_t t = R + m - bij_round(L, B.key[i], m);
-        t = t >= m ? t - m : t;
+        const uint32_t t = bij_reduce(R + m - bij_round(L, B.key[i], m), m);
         R = L;
         L = t;
     }
@@ -106,8 +115,7 @@ BIJ_HD uint32_t bij_dec_tab(const BijParams& B, const TAB& tab, uint32_t y)
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
         const uint32_t m = (i & 1) ? B.b : B.a;
-        uint32_t t = R + m - (uint32_t)tab(i, L);
-        t = t >= m ? t - m : t;
+        const uint32_t t = bij_reduce(R + m - (uint32_t)tab(i, L), m);
         R = L;
         L = t;
     }
@@ -124,8 +132,7 @@ BIJ_HD uint32_t bij_enc_tab(const BijParams& B, const TAB& tab, uint32_t x)
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const uint32_t m = (i & 1) ? B.b : B.a;
-        uint32_t t = L + (uint32_t)tab(i, R);
-        t = t >= m ? t - m : t;
+        const uint32_t t = bij_reduce(L + (uint32_t)tab(i, R), m);
         L = R;
         R = t;
     }
