@@ -114,6 +114,39 @@ template <> struct Math<double> {
     }
 };
 
+// Exchange records of the bijection mode's cluster classes: a particle's velocity
+// and id in one 16-byte (binary32) or 32-byte (binary64) record.  They move
+// between the SMs of a cluster through L2 (.cg: a record another SM wrote is
+// never read from a stale line of this SM's L1).
+template <class T> struct Xg;
+template <> struct Xg<float> {
+    static __device__ __forceinline__ void put(void* b, uint32_t i, float x, float y, float z, uint32_t l)
+    {
+        __stcg(reinterpret_cast<float4*>(b) + i, make_float4(x, y, z, __uint_as_float(l)));
+    }
+    static __device__ __forceinline__ void get(const void* b, uint32_t i, float& x, float& y, float& z, uint32_t& l)
+    {
+        const float4 t = __ldcg(reinterpret_cast<const float4*>(b) + i);
+        x = t.x; y = t.y; z = t.z;
+        l = __float_as_uint(t.w);
+    }
+};
+template <> struct Xg<double> {
+    static __device__ __forceinline__ void put(void* b, uint32_t i, double x, double y, double z, uint32_t l)
+    {
+        double2* p = reinterpret_cast<double2*>(b) + 2 * (size_t)i;
+        __stcg(p, make_double2(x, y));
+        __stcg(p + 1, make_double2(z, __longlong_as_double((long long)l)));
+    }
+    static __device__ __forceinline__ void get(const void* b, uint32_t i, double& x, double& y, double& z, uint32_t& l)
+    {
+        const double2* p = reinterpret_cast<const double2*>(b) + 2 * (size_t)i;
+        const double2 t0 = __ldcg(p), t1 = __ldcg(p + 1);
+        x = t0.x; y = t0.y; z = t1.x;
+        l = (uint32_t)__double_as_longlong(t1.y);
+    }
+};
+
 // Takizuka-Abe binary collision of an equal-mass pair (a, b): the change
 // Delta u of the relative velocity (zero when u = 0); the caller applies
 // v_a += Delta u / 2, v_b -= Delta u / 2.  A is the cell coefficient so that
@@ -596,6 +629,14 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     const unsigned r = Cl<C>::rank();
     const unsigned tid = threadIdx.x;
     DevState* ds = a.ds;
+    // exchange records (bijection mode, clusters): each cluster reuses its own C CAPL
+    // records, which stay in L2, when the grid's share fits in the region (one record per
+    // particle); otherwise a cell uses the records of its own index-list range
+    const bool xg_own = (size_t)gridDim.x * CAPL <= (size_t)a.n_cap;
+    const uint32_t xg_first = (uint32_t)(blockIdx.x - r) * CAPL;
+    // deep exchange loads (staged or XGB in flight per thread) only where registers allow
+    constexpr bool XG_DEEP = NT <= 512;
+    constexpr int XGB = XG_DEEP ? 4 : 1;
     const uint32_t list_n = ds->class_n[a.cls];
     const uint32_t step = ds->step;
     const bool do_coul = (a.flags & F_COULOMB) != 0u;
@@ -667,14 +708,11 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // is pi(hb + k) -- no keys, no sort.
         const uint32_t* bw = reinterpret_cast<const uint32_t*>(a.cpar + (size_t)j * NCP + CP_BIJ);
         const uint32_t bij_ab = __ldg(bw + CPB_AB);
-        // clusters of 8 in the bijection mode gather by pairing position (step 2): no home ids
-        constexpr bool GATHER_BY_POS = C >= 8;
-        const bool home_ids = !GATHER_BY_POS || bij_ab == 0u;
         uint32_t hl[ITEMS], hp[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {   // all id loads in flight before their first use
             const uint32_t k = tid + (uint32_t)i * NT;
-            hl[i] = home_ids && k < nh ? __ldcs(a.perm + s + hb + k) : 0u;
+            hl[i] = k < nh ? __ldcs(a.perm + s + hb + k) : 0u;
             hp[i] = 0u;
         }
         uint32_t multi = 0u;           // items whose bucket holds several entries
@@ -689,7 +727,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             const BijParams B = bij_shape_of();
             if constexpr (C > 1) {
                 // the six round functions as byte tables (round i reads its input below b
-                // for even i, a for odd i), for the position owners' inverse in step 2;
+                // for even i, a for odd i) for the pairing positions of the home particles;
                 // the previous cell's readers passed several barriers
                 for (uint32_t e = tid; e < 6u * 256u; e += NT) {
                     const uint32_t i = e >> 8, v = e & 255u;
@@ -697,17 +735,15 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     if (v < lim) s_rt[i][v] = (uint8_t)bij_round(v, __ldg(bw + CPB_KEY + i), m);
                 }
                 __syncthreads();
-                if constexpr (!GATHER_BY_POS) {      // the home CTA places its particles
 #pragma unroll
-                    for (int i = 0; i < ITEMS; ++i) {
-                        const uint32_t k = tid + (uint32_t)i * NT;
-                        uint32_t y = 0u;
-                        if (k < nh) {
-                            y = bij_enc_tab(B, rt, hb + k);
-                            while (y >= n) y = bij_enc_tab(B, rt, y);
-                        }
-                        hp[i] = y;
+                for (int i = 0; i < ITEMS; ++i) {
+                    const uint32_t k = tid + (uint32_t)i * NT;
+                    uint32_t y = 0u;
+                    if (k < nh) {
+                        y = bij_enc_tab(B, rt, hb + k);
+                        while (y >= n) y = bij_enc_tab(B, rt, y);
                     }
+                    hp[i] = y;
                 }
             } else {                   // (single CTAs: the rounds computed, no tables)
                 BijParams K = B;
@@ -928,32 +964,42 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 }
             }
             cp_async_wait_all();
-        } else if (GATHER_BY_POS && bij_ab != 0u) {
-            // Bijection mode, clusters of 8: each CTA gathers the particles of its own pairing positions
-            // (the inverse bijection gives the id rank, the cell's run or id list the id)
-            // straight from global memory with asynchronous copies, all in flight at once:
-            // in clusters of eight, random reads through L2 sustain a higher rate than
-            // random stores into the other CTAs' shared memory.  Same pair slots as S1.
-            const BijParams B = bij_shape_of();
-            const uint32_t rs = __ldg(a.run_start + j), rl = min(__ldg(a.run_len + j), n);
-            for (uint32_t p = tid; 2u * p < nloc; p += NT) {
+        } else if (bij_ab != 0u) {
+            // Bijection mode, clusters: every CTA sends its home particles' records
+            // (velocity, id) to their pairing positions in the cell's exchange records, one
+            // random 16-byte (binary64: 32-byte) store to L2 each; after the cluster barrier
+            // below every CTA reads its own positions' records in order.  With 512 threads or
+            // fewer (16 warps) the velocities are first staged in this CTA's slots (free until
+            // then), all copies in flight at once; 32 warps hide the loads' latency anyway, and
+            // their 64 registers leave no room for it.
+            const uint32_t xb = xg_own ? xg_first : s;
+            if constexpr (XG_DEEP) {
 #pragma unroll
-                for (uint32_t u = 0; u < 2u; ++u) {
-                    const uint32_t q = 2u * p + u;
-                    if (q < nloc) {
-                        uint32_t x = bij_dec_tab(B, rt, pb + q);
-                        while (x >= n) x = bij_dec_tab(B, rt, x);
-                        const uint32_t l = x < rl ? rs + x : __ldg(a.perm + s + x);
-                        cp_async<sizeof(T)>(svx + q, a.vx + l);
-                        cp_async<sizeof(T)>(svy + q, a.vy + l);
-                        cp_async<sizeof(T)>(svz + q, a.vz + l);
-                        sl[q] = l;
-                        if (a.order_out) a.order_out[s + pb + q] = l;
+                for (int i = 0; i < ITEMS; ++i) {
+                    const uint32_t k = tid + (uint32_t)i * NT;
+                    if (k < nh) {
+                        const uint32_t l = hl[i];
+                        cp_async<sizeof(T)>(svx + k, a.vx + l);
+                        cp_async<sizeof(T)>(svy + k, a.vy + l);
+                        cp_async<sizeof(T)>(svz + k, a.vz + l);
                     }
                 }
+                cp_async_wait_all();
             }
-            cp_async_wait_all();
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t k = tid + (uint32_t)i * NT;
+                if (k < nh) {
+                    const uint32_t l = hl[i];
+                    if constexpr (XG_DEEP) Xg<T>::put(a.xg, xb + hp[i], svx[k], svy[k], svz[k], l);
+                    else Xg<T>::put(a.xg, xb + hp[i], a.vx[l], a.vy[l], a.vz[l], l);
+                    if (a.order_out) a.order_out[s + hp[i]] = l;
+                }
+            }
+            if (!XG_DEEP && tid == 0) cp_async_wait_all();
         } else {
+            // key sort, clusters: the home CTA stores each particle's velocity, id and
+            // candidate word into the position owner's shared memory
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 const uint32_t k = tid + (uint32_t)i * NT;
@@ -966,30 +1012,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     *Cl<C>::at(svx + lp, o) = x;
                     *Cl<C>::at(svy + lp, o) = y;
                     *Cl<C>::at(svz + lp, o) = z;
-                    if (bij_ab == 0u) {
-                        *Cl<C>::at(sl + lp, o) = l;
-                        *Cl<C>::at(sw + lp, o) = (uint16_t)(hp[i] >> 16);
-                    }
+                    *Cl<C>::at(sl + lp, o) = l;
+                    *Cl<C>::at(sw + lp, o) = (uint16_t)(hp[i] >> 16);
                     if (a.order_out) a.order_out[s + pos] = l;
-                }
-            }
-            // Bijection mode: the position owner finds each position's id itself (the
-            // inverse bijection gives the id rank, the cell's run or id list the id)
-            // instead of receiving it: remote stores are the slowest shared-memory
-            // access on this GPU.  Same pair slots as step S1 below, so no barrier between.
-            if (bij_ab != 0u) {
-                const BijParams B = bij_shape_of();
-                const uint32_t rs = __ldg(a.run_start + j), rl = min(__ldg(a.run_len + j), n);
-                for (uint32_t p = tid; 2u * p < nloc; p += NT) {
-#pragma unroll
-                    for (uint32_t u = 0; u < 2u; ++u) {
-                        const uint32_t q = 2u * p + u;
-                        if (q < nloc) {
-                            uint32_t x = bij_dec_tab(B, rt, pb + q);
-                            while (x >= n) x = bij_dec_tab(B, rt, x);
-                            sl[q] = x < rl ? rs + x : __ldg(a.perm + s + x);
-                        }
-                    }
                 }
             }
             if (tid == 0) cp_async_wait_all();
@@ -999,6 +1024,26 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
 #pragma unroll
         for (int i = 0; i < ITEMS / 2; ++i) hq[i] = (hp[2 * i] & 0xFFFFu) | (hp[2 * i + 1] << 16);
         Cl<C>::sync();
+        if constexpr (C > 1) {
+            if (bij_ab != 0u) {   // this CTA's pairing positions, in order, from the exchange records
+                const uint32_t xb = (xg_own ? xg_first : s) + pb;
+                for (uint32_t q0 = tid; q0 < nloc; q0 += (uint32_t)XGB * NT) {
+                    T x[XGB], y[XGB], z[XGB];
+                    uint32_t l[XGB];
+#pragma unroll
+                    for (int u = 0; u < XGB; ++u) {
+                        const uint32_t q = q0 + (uint32_t)u * NT;
+                        if (q < nloc) Xg<T>::get(a.xg, xb + q, x[u], y[u], z[u], l[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < XGB; ++u) {
+                        const uint32_t q = q0 + (uint32_t)u * NT;
+                        if (q < nloc) { svx[q] = x[u]; svy[q] = y[u]; svz[q] = z[u]; sl[q] = l[u]; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
 
         pc.mark(6);
         // The next cell's id list into L2 now, and its first particle id, from
@@ -1459,6 +1504,44 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     a.vx[l] = svx[pos];
                     a.vy[l] = svy[pos];
                     a.vz[l] = svz[pos];
+                }
+            }
+        } else if (bij_ab != 0u) {
+            // bijection mode: each position's record goes back to its home in the exchange
+            // region (particles outside the cell's loaded run straight to their ids), and
+            // after the cluster barrier every CTA writes its home slice in order
+            const uint32_t rs = __ldg(a.run_start + j), rl = min(__ldg(a.run_len + j), n);
+            for (uint32_t q = tid; q < nloc; q += NT) {
+                const uint32_t l = sl[q], k = l - rs;
+                if (k < rl) {
+                    Xg<T>::put(a.xg, (xg_own ? xg_first : s) + k, svx[q], svy[q], svz[q], l);
+                } else {
+                    a.vx[l] = svx[q];
+                    a.vy[l] = svy[q];
+                    a.vz[l] = svz[q];
+                }
+            }
+            Cl<C>::sync();
+            // (16 warps: XGB records per thread in flight before their stores, which the
+            // compiler may not move above the next loads)
+            const uint32_t he = min(hb + nh, rl), xb = xg_own ? xg_first : s;
+            for (uint32_t k0 = hb + tid; k0 < he; k0 += (uint32_t)XGB * NT) {
+                T x[XGB], y[XGB], z[XGB];
+                uint32_t l[XGB];
+#pragma unroll
+                for (int u = 0; u < XGB; ++u) {
+                    const uint32_t k = k0 + (uint32_t)u * NT;
+                    if (k < he) Xg<T>::get(a.xg, xb + k, x[u], y[u], z[u], l[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < XGB; ++u) {
+                    const uint32_t k = k0 + (uint32_t)u * NT;
+                    if (k < he) {
+                        if (l[u] != rs + k) flag_error(ds, ERR_INDEX);
+                        a.vx[rs + k] = x[u];
+                        a.vy[rs + k] = y[u];
+                        a.vz[rs + k] = z[u];
+                    }
                 }
             }
         } else {

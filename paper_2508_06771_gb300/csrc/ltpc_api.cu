@@ -31,7 +31,8 @@ struct Layout {
     size_t vx, vy, vz, cell, x;
     // work offsets
     size_t perm, counts, cell_start, cs_prev, cursor, ion_count, ion_off, stage_l, stage_vx, stage_vy,
-        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, accel, rec_count, xs, lists, ds;
+        stage_vz, mom, hist, inv_vol, dt_factor, lnlam, cpar, run_start, run_len, aslot, accel, rec_count, xs, lists, ds,
+        xg;
 };
 
 bool compute_layout(const ltpc_config* c, Layout* L)
@@ -74,6 +75,9 @@ bool compute_layout(const ltpc_config* c, Layout* L)
     L->xs = take((size_t)2 * XS_MAX_PIECES * 4 * (8 + 4));   // two tables, binary64 then binary32
     L->lists = take(M * 16 * MAX_CLASSES);
     L->ds = take(sizeof(DevState));
+    // bijection mode: the cluster classes' exchange records, one per particle (16 bytes in
+    // binary32, 32 in binary64)
+    L->xg = c->pairing_mode == LTPC_PAIR_BIJECTION ? take(cap * 4 * es) : (size_t)-1;
     L->work = o;
     return true;
 }
@@ -213,6 +217,7 @@ CellArgs<T> make_args(ltpc_ctx* ctx, uint32_t flags)
     a.run_start = ctx->w<uint32_t>(L.run_start);
     a.run_len = ctx->w<uint32_t>(L.run_len);
     a.order_out = nullptr;
+    a.xg = L.xg != (size_t)-1 ? (void*)ctx->w<unsigned char>(L.xg) : nullptr;
     a.phase_clk = nullptr;
     return a;
 }

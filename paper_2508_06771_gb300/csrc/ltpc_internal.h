@@ -129,6 +129,8 @@ struct CellArgs {
     const uint32_t* run_start;   // [M] first index of each cell's loaded run (storage grouped by cell)
     const uint32_t* run_len;     // [M] its length (0: not grouped)
     uint32_t* order_out;         // optional: pairing order written at I_j + position
+    void* xg;                    // bijection mode, clusters: one record {v, id} per particle, at
+                                 // I_j + position, then I_j + home (Xg<T>); null in the key mode
     unsigned long long* phase_clk; // optional: SM cycles spent per kernel phase (tracing)
 };
 
