@@ -792,8 +792,9 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded numpy generator, one replica per rank)",
             "config": {"workload": desc, "cells": wl["M"], "particles_start": int(n0),
-                       "particles_end_of_timed": int(n_end), "precision": f"{prec} velocities and collision "
-                       "arithmetic, f64 per-cell sums", "graph": True,
+                       "particles_end_of_timed": int(n_end), "precision": f"{prec} velocities, collision "
+                       "arithmetic and sums within a CTA; f64 across a cluster's CTAs and in the "
+                       "moments", "graph": True,
                        "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (
                            n0 * (16 if prec == 'f32' else 28) / 1e6),
                        "class_table": [f"C={c['cluster']} x {c['threads']} thr, cells<={c['max_n']}" for c in classes],

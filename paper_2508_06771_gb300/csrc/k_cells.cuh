@@ -27,6 +27,7 @@
 // particles' ids.  Index math is in ltpc_index.h.
 #pragma once
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "bijection.cuh"
 #include "ltpc_index.h"
@@ -357,7 +358,8 @@ __device__ __forceinline__ void for_each_masked(uint32_t* mask, uint32_t nw, uin
 
 // Sum NQ per-thread partials over the cluster in a fixed order: warp
 // butterfly in the working precision (at most 32 x ITEMS values per warp
-// partial), then the warps' partials in double by one warp -- lane l takes
+// partial), then the warps' partials by one warp (in the working precision
+// for a single CTA, in double for a cluster) -- lane l takes
 // quantity l % NQ and every (32 / NQ)-th warp partial, summed as a tree, and
 // the lanes of a quantity are combined by xor shuffles -- and the CTAs in rank
 // order in double.  Deterministic for a given block shape.  With C = 1 only
@@ -391,24 +393,27 @@ __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, 
     __syncthreads();
     if (warp == 0) {
         const unsigned k = lane % NQ, g = lane / NQ;
-        double x[PER];
+        // a single CTA combines its warps' partials in the working precision (binary64 on
+        // the FP64 pipe is the slow part of this serial step), a cluster in double
+        using R = typename std::conditional<C == 1, A, double>::type;
+        R x[PER];
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const unsigned w = g + (unsigned)i * G;
-            x[i] = w < (unsigned)NW ? (double)s_red[w * NQ + k] : 0.0;
+            x[i] = w < (unsigned)NW ? (R)s_red[w * NQ + k] : R(0);
         }
 #pragma unroll
         for (int h = 1; h < PER; h <<= 1) {
 #pragma unroll
             for (int i = 0; i + h < PER; i += 2 * h) x[i] += x[i + h];
         }
-        double t = x[0];
+        R t = x[0];
 #pragma unroll
         for (int o = NQ; o < 32; o <<= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
         if constexpr (C == 1) {
             // a single CTA: warp 0 holds the totals; its callers read them from
             // warp 0 only, so no further barrier
-            if (lane < (unsigned)NQ) out[lane] = 0.0 + t;
+            if (lane < (unsigned)NQ) out[lane] = 0.0 + (double)t;
             __syncwarp();
         } else {
             if (lane < (unsigned)NQ) s_cl[lane] = t;

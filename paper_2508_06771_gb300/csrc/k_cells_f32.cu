@@ -1,5 +1,6 @@
 // k_cells_f32.cu -- float instantiations of the cell kernel (velocities and the
-// collision arithmetic in binary32; per-cell sums combined in double).
+// collision arithmetic in binary32; the sums of a CTA's warps in binary32, of
+// a cluster's CTAs in double).
 #include "k_cells_inst.cuh"
 
 namespace ltpc {

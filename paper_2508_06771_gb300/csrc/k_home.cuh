@@ -279,11 +279,9 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             hx[2 * i] = 2u * p < n ? bij_dec_tab(B, rt, 2u * p) : 0u;
             hx[2 * i + 1] = 2u * p + 1u < n ? bij_dec_tab(B, rt, 2u * p + 1u) : 0u;
         }
-        uint32_t pk[PS];                                   // home indices of positions 2p | 2p+1 << 16
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
             const uint32_t p = tid + (uint32_t)i * NT;
-            pk[i] = 0u;
             if (2u * p < n) {
                 uint32_t ka = hx[2 * i], kb = hx[2 * i + 1];
                 while (ka >= n) ka = bij_dec_tab(B, rt, ka);
@@ -291,7 +289,6 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                 if (two) {
                     while (kb >= n) kb = bij_dec_tab(B, rt, kb);
                 }
-                pk[i] = ka | (kb << 16);
                 sinv[2u * p] = (uint16_t)ka;
                 if (two) sinv[2u * p + 1u] = (uint16_t)kb;
                 if (a.order_out) {                         // inspection: the pairing order of this step
@@ -358,7 +355,9 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
             auto slot = [&](int i) {
                 const uint32_t p = tid + (uint32_t)i * NT;
                 if (2u * p >= n) return;
-                const uint32_t ka = pk[i] & 0xFFFFu, kb = pk[i] >> 16;
+                // the pair's homes from the table (this thread wrote them in step 2)
+                const uint32_t pkv = reinterpret_cast<const uint32_t*>(sinv)[p];
+                const uint32_t ka = pkv & 0xFFFFu, kb = pkv >> 16;
                 if (2u * p + 1u < n) {
                     const uint32_t la = id_of(ka), lb = id_of(kb);
                     V2 X = P::make(svx[ka], svx[kb]);
@@ -388,8 +387,10 @@ __global__ void __launch_bounds__(NT, 1) k_home(CellArgs<T> a)
                 if constexpr (sizeof(T) == 4) {
                     const uint32_t p1 = tid + (uint32_t)(i + 1) * NT;
                     if (i + 1 < PS && 2u * p1 + 1u < n) {       // two full pairs: packed lanes
-                        const uint32_t ka0 = pk[i] & 0xFFFFu, kb0 = pk[i] >> 16;
-                        const uint32_t ka1 = pk[i + 1] & 0xFFFFu, kb1 = pk[i + 1] >> 16;
+                        const uint32_t pk0 = reinterpret_cast<const uint32_t*>(sinv)[tid + (uint32_t)i * NT];
+                        const uint32_t pk1 = reinterpret_cast<const uint32_t*>(sinv)[p1];
+                        const uint32_t ka0 = pk0 & 0xFFFFu, kb0 = pk0 >> 16;
+                        const uint32_t ka1 = pk1 & 0xFFFFu, kb1 = pk1 >> 16;
                         const uint32_t la0 = id_of(ka0), lb0 = id_of(kb0), la1 = id_of(ka1), lb1 = id_of(kb1);
                         V2 AX = P::make(svx[ka0], svx[ka1]), AY = P::make(svy[ka0], svy[ka1]);
                         V2 AZ = P::make(svz[ka0], svz[ka1]);
