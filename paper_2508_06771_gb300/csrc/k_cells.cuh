@@ -426,10 +426,12 @@ __device__ __forceinline__ void cluster_sum(A (&v)[NQ], A* s_red, double* s_cl, 
         for (unsigned q = 0; q < (unsigned)C; ++q) acc += *Cl<C>::at(&s_cl[threadIdx.x], q);
         out[threadIdx.x] = acc;
     }
-    Cl<C>::sync();
+    // s_cl is read remotely until every CTA reaches the next cluster barrier, so the
+    // caller alternates two buffers between consecutive calls (no trailing cluster barrier)
+    __syncthreads();
 }
 
-// Largest value over the cluster (exact in any order).
+// Largest value over the cluster (exact in any order); s_cl as in cluster_sum.
 template <int NT, int C, class A>
 __device__ __forceinline__ A cluster_max(A v, A* s_red, double* s_cl)
 {
@@ -447,8 +449,7 @@ __device__ __forceinline__ A cluster_max(A v, A* s_red, double* s_cl)
     Cl<C>::sync();
     double m = 0.0;
     for (unsigned q = 0; q < (unsigned)C; ++q) m = fmax(m, *Cl<C>::at(&s_cl[0], q));
-    Cl<C>::sync();
-    return (A)m;
+    return (A)m;                                     // (alternating buffers, as cluster_sum)
 }
 
 __device__ __forceinline__ void flag_error(DevState* ds, uint32_t bit) { atomicOr(&ds->err, bit); }
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
 
     __shared__ uint32_t s_scan[NW + 1];
     __shared__ T s_redacc[NW * 8];
-    __shared__ double s_cl[8];
+    __shared__ double s_cl[16];                      // two buffers, alternated between cluster reductions
     __shared__ double s_tot[8];
     __shared__ uint32_t s_hist[4 * NBIN];           // four sub-histograms (less atomic contention)
     __shared__ uint32_t s_cmask[CAPL / 32];         // candidate / work bit masks over local positions
@@ -659,6 +660,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
     Cl<C>::sync();   // every CTA of the cluster is running before any remote access
     PhaseClock pc{a.phase_clk, 0};
     pc.start();
+    uint32_t clb = 0u;                                // cluster reductions so far (buffer parity)
 
     for (uint32_t par = 0u;; par ^= 1u) {
         const uint4 item = s_item[par];
@@ -698,8 +700,18 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         PB.init_pos(n);
         BB.init_split(nb);
 
-        // ---- 1a. zero this CTA's bucket counters and histogram
-        for (uint32_t i = tid; i <= (SB ? n : nbl); i += NT) bcnt[i] = 0u;   // (SB: n + 1 words)
+        // the cell's bijection words (uniform over the cluster; bij_ab == 0: key sort)
+        const uint32_t* bw = reinterpret_cast<const uint32_t*>(a.cpar + (size_t)j * NCP + CP_BIJ);
+        const uint32_t bij_ab = __ldg(bw + CPB_AB);
+        // this cell's exchange records (bijection mode, clusters)
+        const uint32_t xgb = xg_own ? xg_first : s;
+
+        // ---- 1a. zero this CTA's bucket counters (key sort) and histogram.  In the bijection
+        // mode this cluster barrier also separates the previous cell's reads of the exchange
+        // records from this cell's record stores.
+        if (bij_ab == 0u) {
+            for (uint32_t i = tid; i <= (SB ? n : nbl); i += NT) bcnt[i] = 0u;   // (SB: n + 1 words)
+        }
         for (uint32_t i = tid; i < 4u * NBIN; i += NT) s_hist[i] = 0u;
         for (uint32_t i = tid; i < CAPL / 32u; i += NT) { s_imask[i] = 0u; s_dmask[i] = 0u; }
         if (tid == 0) s_vmax = 0u;
@@ -711,8 +723,6 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // the cell's index list is in ascending id order (storage grouped by cell),
         // so home index hb + k is the particle's id rank and its pairing position
         // is pi(hb + k) -- no keys, no sort.
-        const uint32_t* bw = reinterpret_cast<const uint32_t*>(a.cpar + (size_t)j * NCP + CP_BIJ);
-        const uint32_t bij_ab = __ldg(bw + CPB_AB);
         uint32_t hl[ITEMS], hp[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {   // all id loads in flight before their first use
@@ -977,7 +987,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             // fewer (16 warps) the velocities are first staged in this CTA's slots (free until
             // then), all copies in flight at once; 32 warps hide the loads' latency anyway, and
             // their 64 registers leave no room for it.
-            const uint32_t xb = xg_own ? xg_first : s;
+            const uint32_t xb = xgb;
             if constexpr (XG_DEEP) {
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i) {
@@ -1031,7 +1041,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         Cl<C>::sync();
         if constexpr (C > 1) {
             if (bij_ab != 0u) {   // this CTA's pairing positions, in order, from the exchange records
-                const uint32_t xb = (xg_own ? xg_first : s) + pb;
+                const uint32_t xb = xgb + pb;
                 for (uint32_t q0 = tid; q0 < nloc; q0 += (uint32_t)XGB * NT) {
                     T x[XGB], y[XGB], z[XGB];
                     uint32_t l[XGB];
@@ -1129,9 +1139,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                             bx0.x + bx0.y, by0.x + by0.y, bz0.x + bz0.y, bs0.x + bs0.y};
                 if (pre_mom) {
                     T acc4[4] = {acc[0], acc[1], acc[2], acc[3]};
-                    cluster_sum<NT, C, 4, T>(acc4, s_redacc, s_cl, s_tot);
+                    cluster_sum<NT, C, 4, T>(acc4, s_redacc, s_cl + 8u * (clb++ & 1u), s_tot);
                 } else {
-                    cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
+                    cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl + 8u * (clb++ & 1u), s_tot);
                 }
                 // x <- V0 + f (x - V1) = f x + (V0 - f V1), with V = c + S1 / n and
                 // K = S2 - |S1|^2 / n.  The sums are double; the scalars are formed in
@@ -1226,7 +1236,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                     numax = s_par[11]; pnull = s_par[12]; hmin = s_misc[0];
                 }
             } else {
-                const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl);
+                const T md = cluster_max<NT, C, T>(vmax2, s_redacc, s_cl + 8u * (clb++ & 1u));
                 if (tid == 0) bound(md, s_par[11], s_par[12], s_misc[0]);
                 __syncthreads();
                 numax = s_par[11]; pnull = s_par[12]; hmin = s_misc[0];
@@ -1462,7 +1472,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             T acc[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[k] = q[k].x + q[k].y;
-            cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl, s_tot);
+            cluster_sum<NT, C, 8, T>(acc, s_redacc, s_cl + 8u * (clb++ & 1u), s_tot);
             if (r == 0 && tid < (unsigned)NBIN) {
                 uint32_t h = 0u;
                 for (unsigned q = 0; q < (unsigned)C; ++q) {
@@ -1519,17 +1529,24 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             for (uint32_t q = tid; q < nloc; q += NT) {
                 const uint32_t l = sl[q], k = l - rs;
                 if (k < rl) {
-                    Xg<T>::put(a.xg, (xg_own ? xg_first : s) + k, svx[q], svy[q], svz[q], l);
+                    Xg<T>::put(a.xg, xgb + k, svx[q], svy[q], svz[q], l);
                 } else {
                     a.vx[l] = svx[q];
                     a.vy[l] = svy[q];
                     a.vz[l] = svz[q];
                 }
             }
+            if (r == 0 && tid == 0) {        // the next item, before the barrier that publishes it
+                const uint4 it = s_item[par ^ 1u];
+                for (unsigned q = 1; q < (unsigned)C; ++q) *Cl<C>::at(&s_item[par ^ 1u], q) = it;
+            }
+            // This barrier also ends the cell for the cluster: the remote reads of the moments
+            // step are done, and the next cell's record stores come after its first cluster
+            // barrier (step 1a), when every CTA has read this cell's records.
             Cl<C>::sync();
             // (16 warps: XGB records per thread in flight before their stores, which the
             // compiler may not move above the next loads)
-            const uint32_t he = min(hb + nh, rl), xb = xg_own ? xg_first : s;
+            const uint32_t he = min(hb + nh, rl), xb = xgb;
             for (uint32_t k0 = hb + tid; k0 < he; k0 += (uint32_t)XGB * NT) {
                 T x[XGB], y[XGB], z[XGB];
                 uint32_t l[XGB];
@@ -1558,12 +1575,13 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             }
         }
         if constexpr (C > 1) {
-            if (r == 0 && tid == 0) {
+            if (bij_ab == 0u && r == 0 && tid == 0) {
                 const uint4 it = s_item[par ^ 1u];
                 for (unsigned q = 1; q < (unsigned)C; ++q) *Cl<C>::at(&s_item[par ^ 1u], q) = it;
             }
         }
-        Cl<C>::sync();
+        if (C == 1 || bij_ab == 0u) Cl<C>::sync();
+        else __syncthreads();
         pc.mark(10);
     }
 }
