@@ -398,10 +398,10 @@ int ltpc_mlp_subsample_features(ltpc_ctx* ctx, ltpc_mlp* mlp, int32_t per_cell, 
  * library (LTPC_NOALLOC_MAX_CELLS + 64 words on every GPU that loads it, kept
  * until exit); no cudaMalloc, cudaFree or allocating library routine is
  * called.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress).  Every call synchronizes its stream and reads a flag
- * word back, so no call may be made while its stream (or the legacy stream) is
- * being captured into a graph.  Every call shares the array and clears what it uses; calls
- * whose work overlaps on the GPU race.  Synchronizes `cuda_stream` (a
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call synchronizes its stream and reads a flag word back.  Every call
+ * shares the array and clears what it uses; calls whose work overlaps on the
+ * GPU race.  Synchronizes `cuda_stream` (a
  * cudaStream_t, NULL = legacy default stream).  Errors: EINVAL (n < 0,
  * n_cells outside [1, LTPC_NOALLOC_MAX_CELLS], a NULL buffer, or a cell id
  * outside [0, n_cells)), ECUDA. */
