@@ -1078,6 +1078,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
         // optional restoration of the cell's momentum and energy.  The largest
         // squared speed after S1 is tracked for the null-collision bound.
         T vmax2 = T(0);
+        // the restoration's pass folded into the moments' (no neutral step: nothing changes
+        // the velocities between them, and the largest speed is not needed)
+        const bool rest_in_moments = do_coul && n >= 2u && do_corr && !do_neut;
         if (do_coul && n >= 2u) {
             // the cell's scalars in the working precision (A with lnL and dt, and the
             // restoration's state before S1, formed at the start of the pass from the
@@ -1172,6 +1175,9 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 const V2 F = P::make(s_par[4], s_par[4]);
                 const V2 OX = P::make(s_par[5], s_par[5]), OY = P::make(s_par[6], s_par[6]),
                          OZ = P::make(s_par[7], s_par[7]);
+                // without the neutral step the moments loop (step 5) applies the restoration
+                // as it reads the slots: one pass instead of two
+                if (!rest_in_moments)
                 for (uint32_t p = tid; p < nslot; p += NT) {
                     const uint32_t ia = 2u * p;
                     const V2 X = P::fma(F, *reinterpret_cast<const V2*>(svx + ia), OX);
@@ -1192,7 +1198,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
             // A single CTA needs no barrier here: the next reads of these positions
             // are by the same threads (same pair slots), or the neutral step follows
             // (its first action is a barrier).
-            if (C > 1) __syncthreads();
+            if (C > 1 && !rest_in_moments) __syncthreads();
         } else if (do_neut) {
             for (uint32_t q = tid; q < nloc; q += NT) {
                 const T x = svx[q], y = svy[q], z = svz[q];
@@ -1450,11 +1456,26 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1)) k_cells(CellArgs<T> a
                 }
                 Cl<C>::sync();
             }
+            V2 RF = P::make(T(1), T(1)), RX = P::make(T(0), T(0)), RY = RX, RZ = RX;
+            if (rest_in_moments) {
+                RF = P::make(s_par[4], s_par[4]);
+                RX = P::make(s_par[5], s_par[5]); RY = P::make(s_par[6], s_par[6]); RZ = P::make(s_par[7], s_par[7]);
+            }
             for (uint32_t p = tid; 2u * p < nloc; p += NT) {
                 const uint32_t ia = 2u * p;
-                const V2 X = *reinterpret_cast<const V2*>(svx + ia);
-                const V2 Y = *reinterpret_cast<const V2*>(svy + ia);
-                const V2 Z = *reinterpret_cast<const V2*>(svz + ia);
+                V2 X = *reinterpret_cast<const V2*>(svx + ia);
+                V2 Y = *reinterpret_cast<const V2*>(svy + ia);
+                V2 Z = *reinterpret_cast<const V2*>(svz + ia);
+                if (rest_in_moments) {                        // the restoration, as in step 3
+                    X = P::fma(RF, X, RX); Y = P::fma(RF, Y, RY); Z = P::fma(RF, Z, RZ);
+                    if (ia + 1u < nloc) {
+                        *reinterpret_cast<V2*>(svx + ia) = X;
+                        *reinterpret_cast<V2*>(svy + ia) = Y;
+                        *reinterpret_cast<V2*>(svz + ia) = Z;
+                    } else {
+                        svx[ia] = X.x; svy[ia] = Y.x; svz[ia] = Z.x;
+                    }
+                }
                 if (n_rec == 0u) {
                     if (ia + 1u < nloc) accum2(X, Y, Z);
                     else accum(X.x, Y.x, Z.x);
