@@ -107,7 +107,10 @@ typedef struct ltpc_config {
 /* Bytes of the two caller-owned device buffers for `cfg`.
  * state_bytes: particle arrays (vx, vy, vz, cell, optional x) for
  *              cfg->capacity particles.  work_bytes: grouping, staging,
- *              moments and per-cell tables.  Pure host computation. */
+ *              moments and per-cell tables; in LTPC_PAIR_BIJECTION mode also
+ *              one exchange record per particle of capacity (16 bytes in
+ *              LTPC_F32, 32 in LTPC_F64), through which the CTAs of a cluster
+ *              pass a large cell's particles.  Pure host computation. */
 int ltpc_required_bytes(const ltpc_config* cfg, size_t* state_bytes, size_t* work_bytes);
 
 /* Create a context on the current CUDA device.  d_state / d_work: device
